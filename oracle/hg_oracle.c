@@ -99,6 +99,44 @@ void or_eval(int64_t n, const double *mass, const double *xp, const double *vp, 
     }
 }
 
+/* Condition scale of the evaluation sums: for each listed i, sum over j != i of
+ * the norms |a_ij|, |j_ij|, |s_ij| of the pair terms defined above (out: [n_act][3]).
+ * Any summation of the terms in working precision u has an error bounded by a
+ * small multiple of u times these sums. */
+void or_eval_absum(int64_t n, const double *mass, const double *xp, const double *vp, const double *ap,
+                   double eps, int64_t n_act, const int32_t *idx, double *out)
+{
+    for (int64_t q = 0; q < n_act; ++q) {
+        int64_t i = idx[q];
+        double sa = 0.0, sj = 0.0, ss = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i)
+                continue;
+            double r[3], v[3], a[3], A[3], J[3], S[3];
+            for (int k = 0; k < 3; ++k) {
+                r[k] = xp[3 * j + k] - xp[3 * i + k];
+                v[k] = vp[3 * j + k] - vp[3 * i + k];
+                a[k] = ap[3 * j + k] - ap[3 * i + k];
+            }
+            double r2 = dot3(r, r) + eps * eps;
+            double alpha = dot3(r, v) / r2;
+            double beta = (dot3(v, v) + dot3(r, a)) / r2 + alpha * alpha;
+            double r3 = r2 * sqrt(r2);
+            for (int k = 0; k < 3; ++k) {
+                A[k] = mass[j] * r[k] / r3;
+                J[k] = mass[j] * v[k] / r3 - 3.0 * alpha * A[k];
+                S[k] = mass[j] * a[k] / r3 - 6.0 * alpha * J[k] - 3.0 * beta * A[k];
+            }
+            sa += norm3(A);
+            sj += norm3(J);
+            ss += norm3(S);
+        }
+        out[3 * q] = sa;
+        out[3 * q + 1] = sj;
+        out[3 * q + 2] = ss;
+    }
+}
+
 /* Sect. 3 item 3 (correction step), for one particle over a step of length h. */
 void or_correct(double h, const double *x0, const double *v0, const double *a0, const double *j0,
                 const double *s0, const double *a1, const double *j1, const double *s1,
@@ -391,6 +429,13 @@ void or_sys_predict_eval(or_sys *sy, double t, int64_t m, const int32_t *idx, do
 {
     or_predict(sy->n, sy->x, sy->v, sy->a, sy->j, sy->s, sy->c, sy->t, t, sy->xp, sy->vp, sy->ap);
     or_eval(sy->n, sy->m, sy->xp, sy->vp, sy->ap, sy->eps, m, idx, acc, jerk, snap);
+}
+
+/* Predict every particle to t and return the condition scales of the listed particles. */
+void or_sys_predict_absum(or_sys *sy, double t, int64_t m, const int32_t *idx, double *out)
+{
+    or_predict(sy->n, sy->x, sy->v, sy->a, sy->j, sy->s, sy->c, sy->t, t, sy->xp, sy->vp, sy->ap);
+    or_eval_absum(sy->n, sy->m, sy->xp, sy->vp, sy->ap, sy->eps, m, idx, out);
 }
 
 int or_sys_get(or_sys *sy, int field, double *out)

@@ -43,6 +43,7 @@ def lib():
             L = C.CDLL(build())
             L.or_predict.argtypes = [_I64] + [_D] * 7 + [C.c_double] + [_D] * 3
             L.or_eval.argtypes = [_I64, _D, _D, _D, _D, C.c_double, _I64, _I32, _D, _D, _D]
+            L.or_eval_absum.argtypes = [_I64, _D, _D, _D, _D, C.c_double, _I64, _I32, _D]
             L.or_correct.argtypes = [C.c_double] + [_D] * 10
             L.or_interp.argtypes = [C.c_double] + [_D] * 9
             L.or_criterion.argtypes = [C.c_double, C.c_int, _D]
@@ -65,6 +66,7 @@ def lib():
             L.or_sys_advance.restype = _I64
             L.or_sys_energy.argtypes = [C.c_void_p, C.c_double, _D, _D]
             L.or_sys_predict_eval.argtypes = [C.c_void_p, C.c_double, _I64, _I32, _D, _D, _D]
+            L.or_sys_predict_absum.argtypes = [C.c_void_p, C.c_double, _I64, _I32, _D]
             L.or_sys_get.argtypes = [C.c_void_p, C.c_int, _D]
             L.or_sys_set.argtypes = [C.c_void_p, C.c_int, _D]
             L.or_sys_time.argtypes = [C.c_void_p]
@@ -111,6 +113,18 @@ def evaluate(mass, xp, vp, ap, eps, idx=None):
     lib().or_eval(n, _d(mass), _d(xp), _d(vp), _d(ap), float(eps), m, idx.ctypes.data_as(_I32),
                   _d(acc), _d(jerk), _d(snap))
     return acc, jerk, snap
+
+
+def eval_absum(mass, xp, vp, ap, eps, idx=None):
+    """Per listed particle: sums over j of |a_ij|, |j_ij|, |s_ij| (columns 0, 1, 2)."""
+    mass = _f64(mass)
+    xp, vp, ap = (_f64(q, (-1, 3)) for q in (xp, vp, ap))
+    n = mass.shape[0]
+    idx = np.arange(n, dtype=np.int32) if idx is None else np.ascontiguousarray(idx, dtype=np.int32)
+    out = np.empty((idx.shape[0], 3))
+    lib().or_eval_absum(n, _d(mass), _d(xp), _d(vp), _d(ap), float(eps), idx.shape[0],
+                        idx.ctypes.data_as(_I32), _d(out))
+    return out
 
 
 def correct(h, x0, v0, a0, j0, s0, a1, j1, s1):
@@ -206,6 +220,12 @@ class System:
         acc, jerk, snap = (np.empty((m, 3)) for _ in range(3))
         lib().or_sys_predict_eval(self._p, float(t), m, idx.ctypes.data_as(_I32), _d(acc), _d(jerk), _d(snap))
         return acc, jerk, snap
+
+    def predict_absum(self, t, idx):
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        out = np.empty((idx.shape[0], 3))
+        lib().or_sys_predict_absum(self._p, float(t), idx.shape[0], idx.ctypes.data_as(_I32), _d(out))
+        return out
 
     def get(self, field):
         shape = (self.n,) if field in ("mass", "t", "dt") else (self.n, 3)

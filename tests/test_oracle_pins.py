@@ -112,6 +112,23 @@ def test_newton_third_law_all_active():
         assert np.abs(tot).max() < 1e-14 * scale
 
 
+def test_condition_scale_equals_norm_when_terms_are_aligned():
+    """sum_j |a_ij| equals |a_i| when every pair term points the same way (particle
+    at the end of a line of others), and exceeds it otherwise (triangle inequality)."""
+    m = np.array([0.5, 0.25, 0.25])
+    x = np.array([[0.0, 0, 0], [1.0, 0, 0], [3.0, 0, 0]])
+    v = np.array([[0.0, 0, 0], [0.0, 0.5, 0], [0.0, -0.25, 0]])
+    a = np.zeros((3, 3))
+    A, J, S = oracle.evaluate(m, x, v, a, 0.0)
+    sc = oracle.eval_absum(m, x, v, a, 0.0)
+    assert sc[0, 0] == pytest.approx(np.linalg.norm(A[0]), rel=1e-15)
+    assert sc[0, 0] == pytest.approx(0.25 / 1.0 + 0.25 / 9.0, rel=1e-15)
+    assert sc[1, 0] == pytest.approx(0.5 / 1.0 + 0.25 / 4.0, rel=1e-15)   # opposite terms
+    assert sc[1, 0] > np.linalg.norm(A[1])
+    assert np.all(sc[:, 1] >= np.linalg.norm(J, axis=1) * (1 - 1e-15))
+    assert np.all(sc[:, 2] >= np.linalg.norm(S, axis=1) * (1 - 1e-15))
+
+
 def test_eval_subset_equals_full_rows_and_skips_self():
     p = inputs.plummer(50, 3)
     ap = rng.normal(size=(50, 3))
