@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the Hermite block-step engine (acc/jerk/snap interactions/s).
+
+Default workload: the Plummer sphere of N = 65536 equal-mass particles in Henon
+units (seed 2), eps = 1e-4, eta = 0.45, dt_max = 1/16, integrated with power-of-
+two block time steps.  One step = advancing the system by one dt_max: every
+block step in that interval (next-block selection, FP64 prediction, evaluation,
+j-split reduction, FP64 correction with the time-step update) plus the energy
+at the synchronisation time that ends it.  value = sum over block steps of
+m * N (pair evaluations) per second of device time, mixed precision (FP32 pair
+arithmetic, double-single position differences, compensated sums, FP64 state).
+
+The line also carries the FP64 path on the same system over its first 1/8 time
+unit (the plain FP64 job) with both paths' |dE/E| there, the CPU oracle timed on
+a bounded sample, an end-to-end figure through the C ABI with host buffers, the
+evaluation kernel's roofline, sampled SM clocks and the kernel launch count.
+Inputs stay resident in HBM between steps; the FP64 state is 176 B/particle.
+
+--impl reference times the CPU oracle (plain single-threaded C) on a bounded
+sample of the same workload.  Under torchrun each rank runs its own replica
+(seed + rank) on its own GPU: weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "acc/jerk/snap interactions/s and % FP32 peak; mixed vs FP64 GPU at stated |ΔE/E|"
+FLOPS_F32 = 77     # FP32 adds + muls of the pair law per interaction (FMA = 2 flops; rsqrt not counted)
+FLOPS_F64 = 77     # the same count for the FP64 path
+PAPER_FLOPS = 97   # the paper's count per interaction (82 SP + 15 DP)
+NUM_SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=65536)
+    ap.add_argument("--imf", choices=["equal", "salpeter"], default="equal")
+    ap.add_argument("--eps", type=float, default=1e-4)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--interval", type=float, default=1.0 / 16)
+    ap.add_argument("--block-steps", type=int, default=0,
+                    help="if > 0, one step = this many block steps (no energy) instead of one interval")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    step = (f"{a.block_steps} block steps" if a.block_steps > 0 else
+            f"one {a.interval:g} time-unit interval of block steps + energy at its end")
+    return (f"Plummer N={a.n} Henon units, {a.imf} masses (seed {a.seed}), eps={a.eps:g}, eta=0.45, "
+            f"dt_max=1/16, power-of-two block steps; step = {step}")
+
+
+def sm_max_mhz():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"]), "measured"
+    except Exception:
+        return 2070.0, "fallback"
+
+
+def fp32_peak_tflops(mhz):
+    return NUM_SMS * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def fp64_peak_tflops(mhz):
+    return NUM_SMS * 2 * 2 * mhz * 1e6 / 1e12     # 2 DFMA/clk/SM (GB300 nominal 1.25 TFLOP/s)
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device, self.proc, self.path = device, None, None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle on a bounded sample of the workload.
+# ----------------------------------------------------------------------------
+def oracle_sample_step(p, m_sample, eps, h):
+    """An oracle block step restricted to m_sample active particles: predict all N
+    by h, evaluate the sample against all N, correct the sample.  (interactions, s)."""
+    import oracle
+
+    n = p.n
+    z = np.zeros((n, 3))
+    idx = np.linspace(0, n - 1, m_sample).astype(np.int32)
+    t0 = time.perf_counter()
+    xp, vp, ap = oracle.predict(p.pos, p.vel, z, z, z, z, np.zeros(n), h)
+    acc, jerk, snap = oracle.evaluate(p.mass, xp, vp, ap, eps, idx)
+    for q, i in enumerate(idx):
+        oracle.correct(h, p.pos[i], p.vel[i], z[i], z[i], z[i], acc[q], jerk[q], snap[q])
+    return m_sample * n, time.perf_counter() - t0
+
+
+def oracle_sample_size(n, target_interactions=6e8):
+    return int(max(1, min(n, target_interactions // n)))
+
+
+def cpu_baseline(p, eps):
+    m = oracle_sample_size(p.n)
+    inter, sec = oracle_sample_step(p, m, eps, 1.0 / 64)
+    return {"value": inter / sec, "unit": "interactions/s", "cores": 1, "kind": "oracle",
+            "sample": f"one oracle block step with {m} of N={p.n} active (predict all N, evaluate {m}xN, "
+                      f"correct {m}): {sec:.1f} s of single-threaded C FP64"}
+
+
+def run_reference(a, rank):
+    if rank != 0:
+        return
+    from paper_1207_2367_gb300 import inputs
+    p = inputs.plummer(a.n, a.seed, imf=a.imf)
+    m = oracle_sample_size(a.n, 1.2e8)
+    for _ in range(a.warmup):
+        oracle_sample_step(p, m, a.eps, 1.0 / 64)
+    tot_i, tot_s = 0, 0.0
+    for _ in range(a.steps):
+        i, s = oracle_sample_step(p, m, a.eps, 1.0 / 64)
+        tot_i += i
+        tot_s += s
+    v = tot_i / tot_s
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "interactions/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot_s / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "sample": f"each step: oracle block step, {m} of N active"},
+        "cpu_baseline": {"value": v, "unit": "interactions/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: oracle block step with {m} of N={a.n} active"},
+        "e2e": {"value": v, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# Our engine.
+# ----------------------------------------------------------------------------
+def make_ctx(hg, p, a, precision, stream, device, profile=1):
+    opts = hg.hg_default_opts(precision=precision, energy_precision=precision, dt_max=1.0 / 16, device=device,
+                              profile=profile, stream=stream)
+    return hg.hg_init(p.mass, p.pos, p.vel, a.eps, 0.45, opts)
+
+
+class Runner:
+    """Advances a context step by step (interval or fixed block-step count)."""
+
+    def __init__(self, hg, ctx, a):
+        self.hg, self.ctx, self.a, self.t = hg, ctx, a, 0.0
+
+    def step(self):
+        if self.a.block_steps > 0:
+            self.hg.hg_step(self.ctx, self.a.block_steps)
+            self.hg.hg_get_stats(self.ctx)          # synchronizes
+            return None
+        self.t += self.a.interval
+        self.hg.hg_advance(self.ctx, self.t)
+        return self.hg.hg_energy(self.ctx)
+
+
+def roofline(hg, inter, prof, mixed, mhz, kind):
+    eval_s = prof["ms"]["evaluate"] / 1e3
+    peak = fp32_peak_tflops(mhz) if mixed else fp64_peak_tflops(mhz)
+    flops = FLOPS_F32 if mixed else FLOPS_F64
+    ach = inter * flops / eval_s / 1e12 if eval_s > 0 else None
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": (ach / peak) if ach else None, "traffic": None,
+            "kernel": "k_eval<Mixed>" if mixed else "k_eval<F64>",
+            "flops_per_interaction": flops,
+            "peak_note": ((f"FP32 FMA pipe: {NUM_SMS} SMs x 128 lanes x 2 flops" if mixed else
+                           f"FP64 pipe: {NUM_SMS} SMs x 2 DFMA x 2 flops") + f" x {mhz:.0f} MHz ({kind} max clock)"),
+            "eval_share_of_step": eval_s / (sum(prof["ms"].values()) / 1e3) if prof["ms"] else None}
+
+
+def run_ours(a, rank, world, dist):
+    import torch
+    from paper_1207_2367_gb300 import binding as hg
+    from paper_1207_2367_gb300 import inputs
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    hg.load()
+    stream = torch.cuda.Stream()
+    mixed = a.precision == "mixed"
+    prec = hg.HG_MIXED if mixed else hg.HG_FP64
+    p = inputs.plummer(a.n, a.seed + rank, imf=a.imf)
+    ctx = make_ctx(hg, p, a, prec, stream, local)
+    run = Runner(hg, ctx, a)
+    K0, W0 = hg.hg_energy(ctx)
+    E0 = K0 + W0
+    dE_at = {}
+    for w in range(a.warmup):
+        e = run.step()
+        if e is not None and abs(run.t - 0.125) < 1e-15:
+            dE_at["0.125"] = abs((sum(e) - E0) / E0)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # L2 (129 MB) is flushed between timed steps by writing a larger buffer,
+    # outside the per-step event pairs.
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    s0 = hg.hg_get_stats(ctx)
+    hg.hg_get_profile(ctx, reset=True)
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ms = 0.0
+    e = None
+    for _ in range(a.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        e = run.step() or e
+        ev1.record(stream)
+        ev1.synchronize()
+        ms += ev0.elapsed_time(ev1)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    del flush
+    s1 = hg.hg_get_stats(ctx)
+    prof = hg.hg_get_profile(ctx)
+    inter = s1["interactions"] - s0["interactions"]
+    launches = s1["kernels"] - s0["kernels"]
+    if e is None:
+        e = hg.hg_energy(ctx)
+    dE_end = abs((sum(e) - E0) / E0)
+
+    ms_max, inter_tot = ms, inter
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        c = torch.tensor([float(inter)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        inter_tot = int(c.item())
+    value = inter_tot / (ms_max / 1e3)
+    mhz, kind = sm_max_mhz()
+
+    e2e = run_e2e(a, hg, ctx, stream, run) if (not a.no_e2e and rank == 0) else None
+    hg.hg_free(ctx)
+    fp64 = run_fp64_job(a, hg, p, stream, local, mhz, kind) if (mixed and not a.no_fp64 and rank == 0) else None
+    cpu = cpu_baseline(p, a.eps) if (not a.no_cpu_baseline and rank == 0) else None
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if mixed else "f64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "n": a.n,
+                   "precision": ("mixed: f32 pair arithmetic, double-single dr, Kahan f32 sums folded into f64, "
+                                 "f64 state/predictor/corrector" if mixed else "f64 throughout"),
+                   "l2": "flushed between timed steps (256 MB write outside the timed events); "
+                         "inputs resident in HBM",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline(hg, inter, prof, mixed, mhz, kind),
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": int(launches),
+        "block_steps": s1["block_steps"] - s0["block_steps"],
+        "interactions": inter,
+        "dE_over_E": {"t_0.125": dE_at.get("0.125"), "end_of_timed_region": dE_end, "t_end": run.t},
+        "gflops_paper_convention": value * PAPER_FLOPS / 1e9,
+        "sections_ms": prof["ms"],
+        "fp64": fp64,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_e2e(a, hg, ctx, stream, run):
+    """The same metric through the public C ABI with host buffers: every step uploads
+    the state from pinned host memory, advances, reads the energy and the state back."""
+    import torch
+    n = a.n
+    host = {f: torch.empty((n,) if f in ("mass", "t", "dt") else (n, 3), dtype=torch.float64).pin_memory()
+            for f in hg.STATE_FIELDS}
+    t_sys = hg.hg_get_state(ctx, host)
+    nbytes = sum(h.numel() * 8 for h in host.values())
+    s0 = hg.hg_get_stats(ctx)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(a.steps):
+        hg.hg_set_state(ctx, host, t_sys)
+        run.step()
+        t_sys = hg.hg_get_state(ctx, host)
+    wall = time.perf_counter() - w0
+    inter = hg.hg_get_stats(ctx)["interactions"] - s0["interactions"]
+    return {"value": inter / wall, "unit": "interactions/s", "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes + (16 if a.block_steps == 0 else 0), "wall_s": wall}
+
+
+def run_fp64_job(a, hg, p, stream, device, mhz, kind):
+    """The plain FP64 path on the same system from t = 0 to 1/8 (two dt_max
+    intervals, energy at each end), timed as a whole job."""
+    import torch
+    ctx = make_ctx(hg, p, a, hg.HG_FP64, stream, device)
+    try:
+        K0, W0 = hg.hg_energy(ctx)
+        s0 = hg.hg_get_stats(ctx)
+        hg.hg_get_profile(ctx, reset=True)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for k in (1, 2):
+            hg.hg_advance(ctx, k / 16)
+            K1, W1 = hg.hg_energy(ctx)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        s1 = hg.hg_get_stats(ctx)
+        prof = hg.hg_get_profile(ctx)
+        inter = s1["interactions"] - s0["interactions"]
+        return {"workload": "same system, t = 0 to 0.125 (two 1/16 steps, energy at each end)",
+                "value": inter / (ms / 1e3), "unit": "interactions/s", "ms_total": ms,
+                "block_steps": s1["block_steps"] - s0["block_steps"],
+                "dE_over_E_t_0.125": abs((K1 + W1 - K0 - W0) / (K0 + W0)),
+                "roofline": roofline(hg, inter, prof, False, mhz, kind), "sections_ms": prof["ms"]}
+    finally:
+        hg.hg_free(ctx)
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if a.impl == "reference":
+        run_reference(a, rank)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        td.init_process_group("nccl")
+        dist = td
+    try:
+        run_ours(a, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

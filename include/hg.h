@@ -1,0 +1,181 @@
+/*
+ * hg.h -- C ABI of the GB300 (sm_103a) direct-summation engine for the
+ * 6th-order Hermite block-timestep N-body method of Capuzzo-Dolcetta, Spera &
+ * Punzo (HiGPUs, "A fully parallel, high precision, N-body code running on
+ * hybrid computing platforms").
+ *
+ * Conventions shared by every call
+ *  - Units: G = 1.  Indices are 0-based int32.  Vectors are [n][3] row-major
+ *    doubles (x, y, z of particle 0, then particle 1, ...).
+ *  - Pointer arguments may point to host memory or to device memory of the
+ *    context's GPU; the library tells them apart with cudaPointerGetAttributes.
+ *    The caller owns every pointer it passes and may reuse it when the call
+ *    returns: inputs are copied, outputs are written before the return.
+ *  - Every call runs on the context's CUDA stream (hg_opts.stream, else a
+ *    stream the context creates).  Calls that return values in host memory
+ *    synchronize that stream; the others only enqueue work.
+ *  - Every int-returning call returns HG_OK (0) or one of the HG_E* codes;
+ *    hg_last_error() then holds a message.  A failed call leaves the
+ *    integration state as it was, except HG_ECUDA and HG_ETIMEOUT, after which
+ *    the context should be freed.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef HG_H
+#define HG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HG_OK 0
+#define HG_EINVAL 1     /* bad argument (size, pointer, value, order of indices) */
+#define HG_ENOMEM 2     /* device or host allocation failed */
+#define HG_ECUDA 3      /* a CUDA call failed */
+#define HG_ESTATE 4     /* call out of order, or particle not due at the block time */
+#define HG_ETIMEOUT 5   /* a bounded device-side wait expired; results are invalid */
+
+#define HG_FP64 0       /* FP64 pair arithmetic and FP64 sums */
+#define HG_MIXED 1      /* FP32 pair arithmetic, double-single position differences,
+                           compensated FP32 sums folded into FP64; FP64 state */
+
+typedef struct hg_ctx hg_ctx;
+
+/* Options.  Fill with hg_default_opts() and change what you need. */
+typedef struct hg_opts {
+    int32_t precision;        /* HG_FP64 or HG_MIXED for the acc/jerk/snap evaluation */
+    int32_t energy_precision; /* HG_FP64 or HG_MIXED pair arithmetic inside hg_energy */
+    int32_t device;           /* CUDA device ordinal */
+    int32_t tpi;              /* 0 = automatic, else threads sharing one i-particle (1..64, power of 2) */
+    int32_t jsplit;           /* 0 = automatic, else number of j-chunks per i-tile ("Bfactor") */
+    int32_t graph_steps;      /* block steps captured per CUDA graph in hg_step/hg_advance (default 8) */
+    int32_t start_mode;       /* 0 = start-up evaluation in hg_init (default); 1 = none: acc, jerk, snap,
+                                 crackle and t are zero and dt = dt_max until hg_set_state (resume) */
+    int32_t profile;          /* 1 = time the sections of every graph-replayed block step with CUDA
+                                 events (hg_get_profile); adds a synchronization per graph replay */
+    double dt_min;            /* smallest step, power of two (default 2^-25, Sect. 3) */
+    double dt_max;            /* largest step, power of two (default 2^-3, Sect. 3) */
+    double eta_init;          /* accuracy parameter of the first step (p = 4 criterion; default 0.01) */
+    void *stream;             /* cudaStream_t to run on; NULL = the context creates one */
+} hg_opts;
+
+/* The state of every particle at its own time t_i (Sect. 3: r, v, a, jerk, snap,
+ * crackle, individual step).  Caller-allocated arrays of n or [n][3] doubles,
+ * host or device.  t_sys is the last block time the system reached. */
+typedef struct hg_state {
+    double *mass;     /* [n] */
+    double *pos;      /* [n][3] */
+    double *vel;      /* [n][3] */
+    double *acc;      /* [n][3] */
+    double *jerk;     /* [n][3] */
+    double *snap;     /* [n][3] */
+    double *crackle;  /* [n][3] */
+    double *t;        /* [n] */
+    double *dt;       /* [n] power-of-two steps */
+    double t_sys;
+} hg_state;
+
+/* Counters kept on the device. */
+typedef struct hg_stats {
+    int64_t block_steps;   /* block steps taken by hg_step/hg_advance */
+    int64_t interactions;  /* sum over those steps of m * n (pair evaluations incl. j == i) */
+    int64_t last_m;        /* size of the last block */
+    double t_sys;          /* last block time */
+    int64_t kernels;       /* kernel launches issued by the library (graph replays count every node) */
+} hg_stats;
+
+/* Device time of the block-step sections (Table 1: next-block selection,
+ * prediction, evaluation, j-split reduction, correction), accumulated over the
+ * graph-replayed block steps taken with opts.profile = 1. */
+typedef struct hg_profile {
+    double ms[5];          /* next, predict, evaluate, reduce, correct */
+    int64_t block_steps;   /* block steps (including no-op steps past t_end) timed */
+} hg_profile;
+
+/* Fill opts with the defaults listed above. */
+void hg_default_opts(hg_opts *opts);
+
+/* Create a context for n particles (masses [n] > 0, positions and velocities
+ * [n][3], finite), softening eps >= 0 (Sect. 2, softened potential) and
+ * accuracy parameter eta > 0 of the generalized Aarseth criterion (Sect. 3).
+ * Performs the start-up: a full evaluation with every particle active at t = 0,
+ * crackle = 0, first steps from the p = 4 criterion with opts->eta_init,
+ * quantized to powers of two in [dt_min, dt_max].  opts may be NULL.
+ * With eps = 0 particles at the same position exert no force on each other.
+ * Errors: HG_EINVAL, HG_ENOMEM, HG_ECUDA. */
+int hg_init(hg_ctx **out, int64_t n, const double *mass, const double *pos, const double *vel,
+            double eps, double eta, const hg_opts *opts);
+
+/* Table 1, section 1: t_next = min_i (t_i + dt_i) and the ascending indices of
+ * the m particles with t_i + dt_i == t_next.  Makes them the context's current
+ * block.  idx (host or device, capacity cap) receives the list when non-NULL;
+ * a list longer than cap gives HG_EINVAL with *m_out still set. */
+int hg_next_block(hg_ctx *ctx, double *t_next, int32_t *idx, int64_t cap, int64_t *m_out);
+
+/* Sect. 3 item 1: predict positions, velocities and accelerations of all n
+ * particles to time t (Taylor series through crackle), in FP64. */
+int hg_predict(hg_ctx *ctx, double t);
+
+/* Sect. 3 item 2: acceleration, jerk and snap of the m listed particles from
+ * all n predicted particles (direct sum, j != i, softened), in the context's
+ * precision.  idx: strictly increasing, in range, host or device; NULL = the
+ * current block of hg_next_block (then m must equal its size).  acc, jerk,
+ * snap: [m][3] outputs (host or device) or NULL to keep the results on the
+ * device for hg_correct.  Needs a preceding hg_predict.  Errors: HG_EINVAL,
+ * HG_ESTATE (no prediction), HG_ECUDA, HG_ETIMEOUT. */
+int hg_evaluate(hg_ctx *ctx, const int32_t *idx, int64_t m, double *acc, double *jerk, double *snap);
+
+/* Sect. 3 item 3 and the time-step update: correct the particles of the last
+ * hg_evaluate (idx NULL, or the same list), derive crackle from the Hermite
+ * interpolant, take the new step from the p = 6 criterion quantized to powers
+ * of two, and advance their time to the prediction time.  Every listed particle
+ * must satisfy t_i + dt_i == prediction time (HG_ESTATE otherwise). */
+int hg_correct(hg_ctx *ctx, const int32_t *idx, int64_t m);
+
+/* n_steps complete block steps (next block, predict, evaluate, j-split
+ * reduction, correct), entirely on the device and replayed from CUDA graphs;
+ * no host synchronization inside.  Errors: HG_EINVAL, HG_ECUDA. */
+int hg_step(hg_ctx *ctx, int64_t n_steps);
+
+/* Block steps until the next block time would exceed t_end (choose t_end a
+ * multiple of dt_max to end with every particle at t_end).  *steps_out, if
+ * non-NULL, receives the number of block steps taken.  Synchronizes. */
+int hg_advance(hg_ctx *ctx, double t_end, int64_t *steps_out);
+
+/* Kinetic and potential energy (Sect. 2 softened potential, W = -sum_{i<j}
+ * m_i m_j / sqrt(r^2 + eps^2)) of the system predicted to the last block time,
+ * summed in FP64 (pair arithmetic per opts.energy_precision).  Uses its own
+ * buffers: a pending hg_predict/hg_evaluate stays valid.  Synchronizes. */
+int hg_energy(hg_ctx *ctx, double *kinetic, double *potential);
+
+/* Copy the state out (every non-NULL field) / replace it (every field required).
+ * hg_set_state checks: masses > 0, finite values, dt a power of two in
+ * [dt_min, dt_max], t_i a multiple of dt_i; it invalidates any prediction. */
+int hg_get_state(hg_ctx *ctx, hg_state *out);
+int hg_set_state(hg_ctx *ctx, const hg_state *in);
+
+/* Device counters (synchronizes). */
+int hg_get_stats(hg_ctx *ctx, hg_stats *out);
+
+/* Section times accumulated so far (zeros unless opts.profile = 1); reset != 0
+ * clears them after the copy. */
+int hg_get_profile(hg_ctx *ctx, hg_profile *out, int reset);
+
+/* Number of particles of the context. */
+int64_t hg_size(const hg_ctx *ctx);
+
+/* Message of the last failed call on ctx (never NULL; "" if none).  Owned by ctx. */
+const char *hg_last_error(const hg_ctx *ctx);
+
+/* Message of the last failed hg_init on this thread (ctx does not exist then). */
+const char *hg_init_error(void);
+
+/* Release the context and its device memory.  NULL is allowed. */
+void hg_free(hg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HG_H */

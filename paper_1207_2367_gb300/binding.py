@@ -1,0 +1,232 @@
+"""Thin ctypes binding of libhgpu.so with the C ABI's names (include/hg.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Array arguments may be numpy arrays (host) or torch tensors (host or
+CUDA, contiguous, float64 / int32); None passes NULL.  Functions raise HGError
+on a non-zero status.  There is no CPU fallback: load() raises if the library
+cannot be built or loaded.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+HG_OK, HG_EINVAL, HG_ENOMEM, HG_ECUDA, HG_ESTATE, HG_ETIMEOUT = range(6)
+HG_FP64, HG_MIXED = 0, 1
+_NAMES = {1: "HG_EINVAL", 2: "HG_ENOMEM", 3: "HG_ECUDA", 4: "HG_ESTATE", 5: "HG_ETIMEOUT"}
+
+
+class HGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class hg_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("energy_precision", C.c_int32), ("device", C.c_int32),
+                ("tpi", C.c_int32), ("jsplit", C.c_int32), ("graph_steps", C.c_int32),
+                ("start_mode", C.c_int32), ("profile", C.c_int32),
+                ("dt_min", C.c_double), ("dt_max", C.c_double), ("eta_init", C.c_double),
+                ("stream", C.c_void_p)]
+
+
+class hg_state(C.Structure):
+    _fields_ = [(f, C.c_void_p) for f in ("mass", "pos", "vel", "acc", "jerk", "snap", "crackle", "t", "dt")] + [
+        ("t_sys", C.c_double)]
+
+
+class hg_stats(C.Structure):
+    _fields_ = [("block_steps", C.c_int64), ("interactions", C.c_int64), ("last_m", C.c_int64),
+                ("t_sys", C.c_double), ("kernels", C.c_int64)]
+
+
+class hg_profile(C.Structure):
+    _fields_ = [("ms", C.c_double * 5), ("block_steps", C.c_int64)]
+
+
+SECTIONS = ("next", "predict", "evaluate", "reduce", "correct")
+
+
+STATE_FIELDS = ("mass", "pos", "vel", "acc", "jerk", "snap", "crackle", "t", "dt")
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Build (if needed) and load the CUDA library; raises on failure."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or _build.build()
+        L = C.CDLL(path)
+        P, I64, D, I32P = C.c_void_p, C.c_int64, C.c_double, C.c_void_p
+        L.hg_default_opts.argtypes = [C.POINTER(hg_opts)]
+        L.hg_default_opts.restype = None
+        L.hg_init.argtypes = [C.POINTER(P), I64, P, P, P, D, D, C.POINTER(hg_opts)]
+        L.hg_next_block.argtypes = [P, C.POINTER(D), I32P, I64, C.POINTER(I64)]
+        L.hg_predict.argtypes = [P, D]
+        L.hg_evaluate.argtypes = [P, I32P, I64, P, P, P]
+        L.hg_correct.argtypes = [P, I32P, I64]
+        L.hg_step.argtypes = [P, I64]
+        L.hg_advance.argtypes = [P, D, C.POINTER(I64)]
+        L.hg_energy.argtypes = [P, C.POINTER(D), C.POINTER(D)]
+        L.hg_get_state.argtypes = [P, C.POINTER(hg_state)]
+        L.hg_set_state.argtypes = [P, C.POINTER(hg_state)]
+        L.hg_get_stats.argtypes = [P, C.POINTER(hg_stats)]
+        L.hg_get_profile.argtypes = [P, C.POINTER(hg_profile), C.c_int]
+        L.hg_size.argtypes = [P]
+        L.hg_size.restype = I64
+        L.hg_last_error.argtypes = [P]
+        L.hg_last_error.restype = C.c_char_p
+        L.hg_init_error.argtypes = []
+        L.hg_init_error.restype = C.c_char_p
+        L.hg_free.argtypes = [P]
+        L.hg_free.restype = None
+        for name in ("hg_init", "hg_next_block", "hg_predict", "hg_evaluate", "hg_correct", "hg_step",
+                     "hg_advance", "hg_energy", "hg_get_state", "hg_set_state", "hg_get_stats", "hg_get_profile"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _ptr(a, dtype=np.float64):
+    """Raw address of a numpy array or torch tensor (contiguous, dtype checked); None -> NULL."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags.c_contiguous:
+            raise TypeError(f"expected a C-contiguous {np.dtype(dtype)} array")
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor):
+        want = torch.float64 if dtype == np.float64 else torch.int32
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {want} tensor")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(ctx, rc):
+    if rc != HG_OK:
+        raise HGError(rc, load().hg_last_error(ctx).decode())
+
+
+def hg_default_opts(**kw) -> hg_opts:
+    o = hg_opts()
+    load().hg_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if k == "stream":
+            v = getattr(v, "cuda_stream", v)
+        setattr(o, k, v)
+    return o
+
+
+def hg_init(mass, pos, vel, eps, eta, opts: hg_opts | None = None):
+    """Returns a context handle (int)."""
+    n = int(mass.shape[0])
+    ctx = C.c_void_p()
+    rc = load().hg_init(C.byref(ctx), n, _ptr(mass), _ptr(pos), _ptr(vel), float(eps), float(eta),
+                        C.byref(opts) if opts is not None else None)
+    if rc != HG_OK:
+        raise HGError(rc, load().hg_init_error().decode())
+    return ctx.value
+
+
+def hg_next_block(ctx, idx=None):
+    """(t_next, m); fills idx (capacity len(idx)) when given."""
+    t = C.c_double()
+    m = C.c_int64()
+    cap = 0 if idx is None else int(idx.shape[0])
+    _check(ctx, load().hg_next_block(ctx, C.byref(t), _ptr(idx, np.int32), cap, C.byref(m)))
+    return t.value, m.value
+
+
+def hg_predict(ctx, t):
+    _check(ctx, load().hg_predict(ctx, float(t)))
+
+
+def hg_evaluate(ctx, idx, m, acc=None, jerk=None, snap=None):
+    _check(ctx, load().hg_evaluate(ctx, _ptr(idx, np.int32), int(m), _ptr(acc), _ptr(jerk), _ptr(snap)))
+
+
+def hg_correct(ctx, idx, m):
+    _check(ctx, load().hg_correct(ctx, _ptr(idx, np.int32), int(m)))
+
+
+def hg_step(ctx, n_steps):
+    _check(ctx, load().hg_step(ctx, int(n_steps)))
+
+
+def hg_advance(ctx, t_end):
+    k = C.c_int64()
+    _check(ctx, load().hg_advance(ctx, float(t_end), C.byref(k)))
+    return k.value
+
+
+def hg_energy(ctx):
+    K, W = C.c_double(), C.c_double()
+    _check(ctx, load().hg_energy(ctx, C.byref(K), C.byref(W)))
+    return K.value, W.value
+
+
+def hg_get_state(ctx, out: dict):
+    """Fills the arrays of out (keys of STATE_FIELDS; missing keys are skipped); returns t_sys."""
+    st = hg_state()
+    for f in STATE_FIELDS:
+        setattr(st, f, _ptr(out.get(f)))
+    _check(ctx, load().hg_get_state(ctx, C.byref(st)))
+    return st.t_sys
+
+
+def hg_set_state(ctx, state: dict, t_sys: float):
+    st = hg_state()
+    for f in STATE_FIELDS:
+        setattr(st, f, _ptr(state[f]))
+    st.t_sys = float(t_sys)
+    _check(ctx, load().hg_set_state(ctx, C.byref(st)))
+
+
+def hg_get_stats(ctx):
+    s = hg_stats()
+    _check(ctx, load().hg_get_stats(ctx, C.byref(s)))
+    return {"block_steps": s.block_steps, "interactions": s.interactions, "last_m": s.last_m, "t_sys": s.t_sys,
+            "kernels": s.kernels}
+
+
+def hg_get_profile(ctx, reset=False):
+    p = hg_profile()
+    _check(ctx, load().hg_get_profile(ctx, C.byref(p), int(bool(reset))))
+    return {"ms": dict(zip(SECTIONS, list(p.ms))), "block_steps": p.block_steps}
+
+
+def hg_size(ctx):
+    return load().hg_size(ctx)
+
+
+def hg_last_error(ctx):
+    return load().hg_last_error(ctx).decode()
+
+
+def hg_free(ctx):
+    if ctx:
+        load().hg_free(ctx)
+
+
+def new_state(n: int, like=None):
+    """Host (numpy) or, with like=a torch device, CUDA arrays for hg_get_state."""
+    shapes = {f: ((n,) if f in ("mass", "t", "dt") else (n, 3)) for f in STATE_FIELDS}
+    if like is None:
+        return {f: np.empty(s) for f, s in shapes.items()}
+    import torch
+    return {f: torch.empty(s, dtype=torch.float64, device=like) for f, s in shapes.items()}

@@ -1,0 +1,720 @@
+// hg_api.cu -- the C ABI of include/hg.h: context, device buffers, the
+// explicit calls of one block step and the graph-captured device-resident
+// stepping loop.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hg.h"
+#include "hg_internal.cuh"
+#include "hg_kernels.cuh"
+
+using namespace hg;
+
+struct hg_ctx {
+    int64_t n = 0, npad = 0;
+    bool mixed = false;
+    double eps = 0.0, eta = 0.0;
+    hg_opts opts{};
+    int device = 0, num_sms = 0, egrid = 0;
+    cudaStream_t stream = nullptr, cap_stream = nullptr;
+    bool own_stream = false;
+    State st{}, st2{};
+    Records rec{};
+    int32_t *d_idx = nullptr, *d_idx2 = nullptr, *nb_cnt = nullptr;
+    double *nb_part = nullptr;
+    DevScalars *d_sc = nullptr, *h_sc = nullptr;   // h_sc: pinned host mirror
+    double *h_stage = nullptr;                     // pinned staging for small uploads
+    double *partial = nullptr;
+    int64_t pcap = 0;
+    double *ra = nullptr, *rj = nullptr, *rs = nullptr;
+    double *xe = nullptr, *ve = nullptr, *phi_part = nullptr, *e_part = nullptr, *e_out = nullptr;
+    int e_splits = 0, e_g2 = 0;
+    cudaGraphExec_t g_one = nullptr, g_many = nullptr;
+    int64_t kernels = 0;            // kernel launches issued (graph replays count every node)
+    std::vector<cudaEvent_t> ev_one, ev_many;   // profile: 6 events per captured block step
+    double prof_ms[5] = {0, 0, 0, 0, 0};
+    int64_t prof_steps = 0;
+    double t_pred = NAN;    // time of the last hg_predict (NaN: none valid)
+    int64_t cur_m = -1;     // size of the block from hg_next_block (-1: none)
+    int64_t eval_m = -1;    // size of the last hg_evaluate (-1: none pending)
+    double eval_t = NAN;
+    std::vector<void *> dev_allocs;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_init_err;
+
+int fail(hg_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+#define HG_CUDA(ctx, call)                                                                        \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return fail((ctx), HG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+bool is_pow2(double x)
+{
+    int e;
+    return x > 0.0 && isfinite(x) && frexp(x, &e) == 0.5;
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+T *dalloc(hg_ctx *c, int64_t count)
+{
+    void *p = nullptr;
+    if (count < 1) count = 1;
+    if (cudaMalloc(&p, (size_t)count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    c->dev_allocs.push_back(p);
+    return static_cast<T *>(p);
+}
+
+bool alloc_state(hg_ctx *c, State &s)
+{
+    const int64_t n = c->n;
+    s.mass = dalloc<double>(c, n);
+    s.t = dalloc<double>(c, n);
+    s.dt = dalloc<double>(c, n);
+    s.x = dalloc<double>(c, 3 * n);
+    s.v = dalloc<double>(c, 3 * n);
+    s.a = dalloc<double>(c, 3 * n);
+    s.j = dalloc<double>(c, 3 * n);
+    s.s = dalloc<double>(c, 3 * n);
+    s.c = dalloc<double>(c, 3 * n);
+    return s.mass && s.t && s.dt && s.x && s.v && s.a && s.j && s.s && s.c;
+}
+
+StepParams step_params(const hg_ctx *c)
+{
+    StepParams p;
+    p.eta = c->eta;
+    p.eta_init = c->opts.eta_init;
+    p.dt_min = c->opts.dt_min;
+    p.dt_max = c->opts.dt_max;
+    return p;
+}
+
+EvalArgs eval_args(hg_ctx *c, const int64_t *m_dev, int64_t m_host)
+{
+    EvalArgs a;
+    a.rec = c->rec;
+    a.npad = c->npad;
+    a.idx = c->d_idx;
+    a.m_dev = m_dev;
+    a.m_host = m_host;
+    a.partial = c->partial;
+    a.pcap = c->pcap;
+    a.eps2 = c->eps * c->eps;
+    a.guard = c->eps == 0.0 ? 1 : 0;
+    a.tpi_force = c->opts.tpi;
+    a.b_force = c->opts.jsplit;
+    a.plan_grid = c->egrid;
+    a.err = &c->d_sc->err;
+    return a;
+}
+
+int tile_j(const hg_ctx *c) { return c->mixed ? kTJMixed : kTJF64; }
+int i_per_thread(const hg_ctx *c) { return c->mixed ? kIMixed : kIF64; }
+
+// Evaluation of the list in d_idx (host-known size m) into ra/rj/rs.
+int run_eval_host_m(hg_ctx *c, int64_t m)
+{
+    EvalArgs a = eval_args(c, nullptr, m);
+    const Plan p = make_plan(m, c->npad / tile_j(c), i_per_thread(c), c->egrid, a.tpi_force, a.b_force, a.pcap);
+    const int grid = (int)(p.n_items < c->egrid ? p.n_items : c->egrid);
+    HG_CUDA(c, launch_eval(c->mixed, a, grid, c->stream));
+    HG_CUDA(c, launch_reduce(c->mixed, a, c->egrid, c->ra, c->rj, c->rs, c->stream));
+    c->kernels += 2;
+    return HG_OK;
+}
+
+int sync_scalars(hg_ctx *c)
+{
+    HG_CUDA(c, cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    HG_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->h_sc->err & ERR_TIMEOUT) return fail(c, HG_ETIMEOUT, "a bounded device wait expired");
+    return HG_OK;
+}
+
+// Reset the validation flag, run a check, read it back.
+template <class F>
+int device_check(hg_ctx *c, F launch, int32_t *flag_out)
+{
+    HG_CUDA(c, cudaMemsetAsync(&c->d_sc->flag, 0, sizeof(int32_t), c->stream));
+    HG_CUDA(c, launch(&c->d_sc->flag));
+    c->kernels += 1;
+    int rc = sync_scalars(c);
+    if (rc) return rc;
+    *flag_out = c->h_sc->flag;
+    return HG_OK;
+}
+
+int upload_scalar(hg_ctx *c, double *dev_field, double v)
+{
+    HG_CUDA(c, cudaStreamSynchronize(c->stream));   // staging buffer is free
+    c->h_stage[0] = v;
+    HG_CUDA(c, cudaMemcpyAsync(dev_field, c->h_stage, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    HG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HG_OK;
+}
+
+constexpr int kStepKernels = 7;   // 3 next-block passes, predict, evaluate, reduce, correct
+
+// An event record that becomes a graph node when the stream is being captured
+// (a plain record inside a capture only orders work and cannot be timed).
+cudaError_t record_external(cudaEvent_t e, cudaStream_t s)
+{
+    return cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+}
+
+// One block step (Table 1 sections 1-4 and 8), sizes read on the device.
+// ev: 6 events bracketing the 5 sections, or nullptr.
+int enqueue_block_step(hg_ctx *c, cudaStream_t s, const cudaEvent_t *ev)
+{
+    if (ev) HG_CUDA(c, record_external(ev[0], s));
+    HG_CUDA(c, launch_next_block(c->st, c->n, c->nb_part, c->nb_cnt, c->d_idx, c->d_sc, 1, s));
+    if (ev) HG_CUDA(c, record_external(ev[1], s));
+    HG_CUDA(c, launch_predict(c->mixed, c->st, c->rec, c->n, c->npad, &c->d_sc->t_cur, 0.0, &c->d_sc->m, s));
+    if (ev) HG_CUDA(c, record_external(ev[2], s));
+    EvalArgs a = eval_args(c, &c->d_sc->m, 0);
+    HG_CUDA(c, launch_eval(c->mixed, a, c->egrid, s));
+    if (ev) HG_CUDA(c, record_external(ev[3], s));
+    HG_CUDA(c, launch_reduce(c->mixed, a, c->egrid, c->ra, c->rj, c->rs, s));
+    if (ev) HG_CUDA(c, record_external(ev[4], s));
+    HG_CUDA(c, launch_correct(c->st, c->d_idx, &c->d_sc->m, 0, c->n, c->ra, c->rj, c->rs, step_params(c), s));
+    if (ev) HG_CUDA(c, record_external(ev[5], s));
+    return HG_OK;
+}
+
+int capture(hg_ctx *c, int steps, cudaGraphExec_t *out, std::vector<cudaEvent_t> &ev)
+{
+    cudaGraph_t g = nullptr;
+    if (c->opts.profile && ev.empty()) {
+        ev.resize((size_t)steps * 6);
+        for (auto &e : ev) HG_CUDA(c, cudaEventCreate(&e));
+    }
+    HG_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = HG_OK;
+    for (int k = 0; k < steps && rc == HG_OK; ++k)
+        rc = enqueue_block_step(c, c->cap_stream, c->opts.profile ? &ev[(size_t)k * 6] : nullptr);
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (rc != HG_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(c, HG_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(c, HG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    return HG_OK;
+}
+
+int ensure_graphs(hg_ctx *c)
+{
+    int rc = HG_OK;
+    if (!c->g_one) rc = capture(c, 1, &c->g_one, c->ev_one);
+    if (rc == HG_OK && !c->g_many) rc = capture(c, c->opts.graph_steps, &c->g_many, c->ev_many);
+    return rc;
+}
+
+// Launch one captured graph; with profiling, wait for it and add its section times.
+int replay(hg_ctx *c, bool many)
+{
+    HG_CUDA(c, cudaGraphLaunch(many ? c->g_many : c->g_one, c->stream));
+    const int steps = many ? c->opts.graph_steps : 1;
+    c->kernels += (int64_t)kStepKernels * steps;
+    if (!c->opts.profile) return HG_OK;
+    HG_CUDA(c, cudaStreamSynchronize(c->stream));
+    const std::vector<cudaEvent_t> &ev = many ? c->ev_many : c->ev_one;
+    for (int k = 0; k < steps; ++k)
+        for (int q = 0; q < 5; ++q) {
+            float ms = 0.f;
+            HG_CUDA(c, cudaEventElapsedTime(&ms, ev[(size_t)k * 6 + q], ev[(size_t)k * 6 + q + 1]));
+            c->prof_ms[q] += ms;
+        }
+    c->prof_steps += steps;
+    return HG_OK;
+}
+
+void invalidate(hg_ctx *c)
+{
+    c->t_pred = NAN;
+    c->cur_m = -1;
+    c->eval_m = -1;
+    c->eval_t = NAN;
+}
+
+void release(hg_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->g_one) cudaGraphExecDestroy(c->g_one);
+    if (c->g_many) cudaGraphExecDestroy(c->g_many);
+    for (cudaEvent_t e : c->ev_one) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->ev_many) cudaEventDestroy(e);
+    for (void *p : c->dev_allocs) cudaFree(p);
+    if (c->h_sc) cudaFreeHost(c->h_sc);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    cudaGetLastError();
+    delete c;
+}
+
+int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *vel)
+{
+    const int64_t n = c->n;
+    HG_CUDA(c, cudaSetDevice(c->device));
+    cudaDeviceProp prop;
+    HG_CUDA(c, cudaGetDeviceProperties(&prop, c->device));
+    c->num_sms = prop.multiProcessorCount;
+    if (c->opts.stream) {
+        c->stream = static_cast<cudaStream_t>(c->opts.stream);
+    } else {
+        HG_CUDA(c, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    HG_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    HG_CUDA(c, cudaMallocHost(reinterpret_cast<void **>(&c->h_sc), sizeof(DevScalars)));
+    HG_CUDA(c, cudaMallocHost(reinterpret_cast<void **>(&c->h_stage), 4 * sizeof(double)));
+
+    const int64_t tj = kTJMixed > kTJF64 ? kTJMixed : kTJF64;
+    c->npad = (n + tj - 1) / tj * tj;
+    bool ok = alloc_state(c, c->st) && alloc_state(c, c->st2);
+    if (c->mixed) {
+        c->rec.p[0] = dalloc<float4>(c, c->npad);
+        c->rec.p[1] = dalloc<float4>(c, c->npad);
+        c->rec.p[2] = dalloc<float4>(c, c->npad);
+        c->rec.p[3] = dalloc<float>(c, c->npad);
+        c->rec.p[4] = nullptr;
+        ok = ok && c->rec.p[0] && c->rec.p[1] && c->rec.p[2] && c->rec.p[3];
+    } else {
+        for (int q = 0; q < 5; ++q) {
+            c->rec.p[q] = dalloc<double2>(c, c->npad);
+            ok = ok && c->rec.p[q];
+        }
+    }
+    c->d_idx = dalloc<int32_t>(c, n);
+    c->d_idx2 = dalloc<int32_t>(c, n);
+    const int g = nb_grid(n);
+    c->nb_part = dalloc<double>(c, g);
+    c->nb_cnt = dalloc<int32_t>(c, g);
+    c->d_sc = dalloc<DevScalars>(c, 1);
+    // Partial sums: b * m <= pcap (b never exceeds the number of j-tiles).
+    const int64_t max_tiles = c->npad / (tile_j(c));
+    int64_t pcap = 4 * n > (1 << 20) ? 4 * n : (1 << 20);
+    if (pcap > max_tiles * n) pcap = max_tiles * n;
+    c->pcap = pcap;
+    c->partial = dalloc<double>(c, 9 * pcap);
+    c->ra = dalloc<double>(c, 3 * n);
+    c->rj = dalloc<double>(c, 3 * n);
+    c->rs = dalloc<double>(c, 3 * n);
+    c->xe = dalloc<double>(c, 3 * n);
+    c->ve = dalloc<double>(c, 3 * n);
+    c->e_splits = energy_splits(n, c->num_sms);
+    c->phi_part = dalloc<double>(c, (int64_t)c->e_splits * n);
+    c->e_g2 = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+    c->e_part = dalloc<double>(c, 2 * c->e_g2);
+    c->e_out = dalloc<double>(c, 2);
+    ok = ok && c->d_idx && c->d_idx2 && c->nb_part && c->nb_cnt && c->d_sc && c->partial && c->ra && c->rj &&
+         c->rs && c->xe && c->ve && c->phi_part && c->e_part && c->e_out;
+    if (!ok) return fail(c, HG_ENOMEM, "device allocation failed");
+
+    HG_CUDA(c, eval_setup(c->device));
+    c->egrid = eval_grid(c->mixed, c->num_sms);
+
+    DevScalars z{};
+    z.t_stop = INFINITY;
+    *c->h_sc = z;
+    HG_CUDA(c, cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(DevScalars), cudaMemcpyHostToDevice, c->stream));
+    HG_CUDA(c, cudaMemcpyAsync(c->st.mass, mass, n * sizeof(double), cudaMemcpyDefault, c->stream));
+    HG_CUDA(c, cudaMemcpyAsync(c->st.x, pos, 3 * n * sizeof(double), cudaMemcpyDefault, c->stream));
+    HG_CUDA(c, cudaMemcpyAsync(c->st.v, vel, 3 * n * sizeof(double), cudaMemcpyDefault, c->stream));
+    int32_t flag = 0;
+    int rc = device_check(
+        c, [&](int32_t *f) { return launch_validate_init(c->st.mass, c->st.x, c->st.v, n, f, c->stream); }, &flag);
+    if (rc) return rc;
+    if (flag) return fail(c, HG_EINVAL, "masses must be finite and > 0, positions and velocities finite");
+
+    // Start-up: every particle active at t = 0; the prediction is the identity.
+    for (double *p : {c->st.a, c->st.j, c->st.s, c->st.c})
+        HG_CUDA(c, cudaMemsetAsync(p, 0, 3 * n * sizeof(double), c->stream));
+    HG_CUDA(c, cudaMemsetAsync(c->st.t, 0, n * sizeof(double), c->stream));
+    if (c->opts.start_mode == 1) {
+        std::vector<double> dtv((size_t)n, c->opts.dt_max);
+        HG_CUDA(c, cudaMemcpyAsync(c->st.dt, dtv.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        rc = sync_scalars(c);
+        if (rc) return rc;
+        invalidate(c);
+        return HG_OK;
+    }
+    std::vector<int32_t> iota((size_t)n);
+    for (int64_t i = 0; i < n; ++i) iota[(size_t)i] = (int32_t)i;
+    HG_CUDA(c, cudaMemcpyAsync(c->d_idx, iota.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    HG_CUDA(c, launch_predict(c->mixed, c->st, c->rec, n, c->npad, nullptr, 0.0, nullptr, c->stream));
+    rc = run_eval_host_m(c, n);
+    if (rc) return rc;
+    HG_CUDA(c, launch_start(c->st, n, c->ra, c->rj, c->rs, step_params(c), c->stream));
+    rc = sync_scalars(c);
+    if (rc) return rc;
+    invalidate(c);
+    return HG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hg_default_opts(hg_opts *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->precision = HG_FP64;
+    o->energy_precision = HG_FP64;
+    o->device = 0;
+    o->tpi = 0;
+    o->jsplit = 0;
+    o->graph_steps = 8;
+    o->start_mode = 0;
+    o->profile = 0;
+    o->dt_min = 1.0 / 33554432.0;   // 2^-25
+    o->dt_max = 0.125;              // 2^-3
+    o->eta_init = 0.01;
+    o->stream = nullptr;
+}
+
+const char *hg_init_error(void) { return g_init_err.c_str(); }
+
+int hg_init(hg_ctx **out, int64_t n, const double *mass, const double *pos, const double *vel, double eps,
+            double eta, const hg_opts *opts)
+{
+    g_init_err.clear();
+    auto bad = [](const char *m) {
+        g_init_err = m;
+        return HG_EINVAL;
+    };
+    if (!out) return bad("out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > (int64_t)INT32_MAX - 1024) return bad("n must be in [1, 2^31 - 1025]");
+    if (!mass || !pos || !vel) return bad("mass, pos and vel are required");
+    if (!isfinite(eps) || eps < 0.0) return bad("eps must be finite and >= 0");
+    if (!isfinite(eta) || eta <= 0.0) return bad("eta must be finite and > 0");
+    hg_opts o;
+    if (opts)
+        o = *opts;
+    else
+        hg_default_opts(&o);
+    if (o.precision != HG_FP64 && o.precision != HG_MIXED) return bad("precision must be HG_FP64 or HG_MIXED");
+    if (o.energy_precision != HG_FP64 && o.energy_precision != HG_MIXED) return bad("bad energy_precision");
+    if (!is_pow2(o.dt_min) || !is_pow2(o.dt_max) || o.dt_min > o.dt_max)
+        return bad("dt_min and dt_max must be powers of two with dt_min <= dt_max");
+    if (!isfinite(o.eta_init) || o.eta_init <= 0.0) return bad("eta_init must be finite and > 0");
+    if (o.tpi != 0 && (o.tpi < 0 || o.tpi > kMaxTPI || (o.tpi & (o.tpi - 1)) != 0))
+        return bad("tpi must be 0 or a power of two <= 64");
+    if (o.jsplit < 0) return bad("jsplit must be >= 0");
+    if (o.graph_steps < 1 || o.graph_steps > 1024) return bad("graph_steps must be in [1, 1024]");
+    if (o.start_mode != 0 && o.start_mode != 1) return bad("start_mode must be 0 or 1");
+
+    hg_ctx *c = new (std::nothrow) hg_ctx();
+    if (!c) {
+        g_init_err = "host allocation failed";
+        return HG_ENOMEM;
+    }
+    c->n = n;
+    c->mixed = o.precision == HG_MIXED;
+    c->eps = eps;
+    c->eta = eta;
+    c->opts = o;
+    c->device = o.device;
+    int rc = init_impl(c, mass, pos, vel);
+    if (rc != HG_OK) {
+        g_init_err = c->err;
+        release(c);
+        return rc;
+    }
+    *out = c;
+    return HG_OK;
+}
+
+int hg_next_block(hg_ctx *c, double *t_next, int32_t *idx, int64_t cap, int64_t *m_out)
+{
+    if (!c) return HG_EINVAL;
+    HG_CUDA(c, launch_next_block(c->st, c->n, c->nb_part, c->nb_cnt, c->d_idx, c->d_sc, 0, c->stream));
+    c->kernels += 3;
+    int rc = sync_scalars(c);
+    if (rc) return rc;
+    const int64_t m = c->h_sc->m;
+    invalidate(c);
+    c->cur_m = m;
+    if (t_next) *t_next = c->h_sc->t_cur;
+    if (m_out) *m_out = m;
+    if (idx) {
+        if (cap < m) return fail(c, HG_EINVAL, "idx capacity smaller than the block");
+        HG_CUDA(c, cudaMemcpyAsync(idx, c->d_idx, m * sizeof(int32_t), cudaMemcpyDefault, c->stream));
+        HG_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return HG_OK;
+}
+
+int hg_predict(hg_ctx *c, double t)
+{
+    if (!c) return HG_EINVAL;
+    if (!isfinite(t)) return fail(c, HG_EINVAL, "t must be finite");
+    HG_CUDA(c, launch_predict(c->mixed, c->st, c->rec, c->n, c->npad, nullptr, t, nullptr, c->stream));
+    c->kernels += 1;
+    c->t_pred = t;
+    c->eval_m = -1;
+    return HG_OK;
+}
+
+int hg_evaluate(hg_ctx *c, const int32_t *idx, int64_t m, double *acc, double *jerk, double *snap)
+{
+    if (!c) return HG_EINVAL;
+    if (isnan(c->t_pred)) return fail(c, HG_ESTATE, "hg_evaluate needs a preceding hg_predict");
+    if (m < 0 || m > c->n) return fail(c, HG_EINVAL, "m must be in [0, n]");
+    if (!idx) {
+        if (c->cur_m < 0 || m != c->cur_m) return fail(c, HG_EINVAL, "idx NULL needs m equal to the current block");
+    } else if (m > 0) {
+        if (is_device_ptr(idx)) {
+            HG_CUDA(c, cudaMemcpyAsync(c->d_idx2, idx, m * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
+            int32_t flag = 0;
+            int rc = device_check(
+                c, [&](int32_t *f) { return launch_validate_idx(c->d_idx2, m, c->n, f, c->stream); }, &flag);
+            if (rc) return rc;
+            if (flag) return fail(c, HG_EINVAL, "idx must be strictly increasing and in [0, n)");
+        } else {
+            for (int64_t q = 0; q < m; ++q)
+                if (idx[q] < 0 || idx[q] >= c->n || (q > 0 && idx[q] <= idx[q - 1]))
+                    return fail(c, HG_EINVAL, "idx must be strictly increasing and in [0, n)");
+            HG_CUDA(c, cudaMemcpyAsync(c->d_idx2, idx, m * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+        }
+        int32_t *t = c->d_idx;
+        c->d_idx = c->d_idx2;
+        c->d_idx2 = t;
+        c->cur_m = m;
+        // Graphs captured the old list pointer: rebuild them on next use.
+        if (c->g_one) { cudaGraphExecDestroy(c->g_one); c->g_one = nullptr; }
+        if (c->g_many) { cudaGraphExecDestroy(c->g_many); c->g_many = nullptr; }
+    }
+    if (m > 0) {
+        int rc = run_eval_host_m(c, m);
+        if (rc) return rc;
+        double *outs[3] = {acc, jerk, snap};
+        const double *res[3] = {c->ra, c->rj, c->rs};
+        for (int k = 0; k < 3; ++k)
+            if (outs[k])
+                HG_CUDA(c, cudaMemcpyAsync(outs[k], res[k], 3 * m * sizeof(double), cudaMemcpyDefault, c->stream));
+    }
+    int rc = sync_scalars(c);
+    if (rc) return rc;
+    c->eval_m = m;
+    c->eval_t = c->t_pred;
+    return HG_OK;
+}
+
+int hg_correct(hg_ctx *c, const int32_t *idx, int64_t m)
+{
+    if (!c) return HG_EINVAL;
+    if (c->eval_m < 0) return fail(c, HG_ESTATE, "hg_correct needs a preceding hg_evaluate");
+    if (m != c->eval_m) return fail(c, HG_EINVAL, "m differs from the last hg_evaluate");
+    if (m == 0) {
+        c->eval_m = -1;
+        return HG_OK;
+    }
+    const int32_t *given = nullptr;
+    if (idx) {
+        HG_CUDA(c, cudaMemcpyAsync(c->d_idx2, idx, m * sizeof(int32_t), cudaMemcpyDefault, c->stream));
+        given = c->d_idx2;
+    }
+    int32_t flag = 0;
+    int rc = device_check(
+        c, [&](int32_t *f) { return launch_check_correct(c->st, given, c->d_idx, m, c->eval_t, f, c->stream); },
+        &flag);
+    if (rc) return rc;
+    if (flag)
+        return fail(c, HG_ESTATE, "list differs from the evaluation, or a particle is not due at the block time");
+    HG_CUDA(c, launch_correct(c->st, c->d_idx, nullptr, m, m, c->ra, c->rj, c->rs, step_params(c), c->stream));
+    c->kernels += 1;
+    rc = upload_scalar(c, &c->d_sc->t_cur, c->eval_t);
+    if (rc) return rc;
+    invalidate(c);
+    return HG_OK;
+}
+
+int hg_step(hg_ctx *c, int64_t n_steps)
+{
+    if (!c) return HG_EINVAL;
+    if (n_steps < 0) return fail(c, HG_EINVAL, "n_steps must be >= 0");
+    if (n_steps == 0) return HG_OK;
+    int rc = ensure_graphs(c);
+    if (rc) return rc;
+    invalidate(c);
+    const int64_t s = c->opts.graph_steps;
+    for (int64_t k = 0; k < n_steps / s; ++k)
+        if ((rc = replay(c, true)) != HG_OK) return rc;
+    for (int64_t k = 0; k < n_steps % s; ++k)
+        if ((rc = replay(c, false)) != HG_OK) return rc;
+    return HG_OK;
+}
+
+int hg_advance(hg_ctx *c, double t_end, int64_t *steps_out)
+{
+    if (!c) return HG_EINVAL;
+    if (!isfinite(t_end)) return fail(c, HG_EINVAL, "t_end must be finite");
+    int rc = ensure_graphs(c);
+    if (rc) return rc;
+    invalidate(c);
+    rc = sync_scalars(c);
+    if (rc) return rc;
+    const int64_t steps0 = c->h_sc->steps;
+    rc = upload_scalar(c, &c->d_sc->t_stop, t_end);
+    if (rc) return rc;
+    HG_CUDA(c, cudaMemsetAsync(&c->d_sc->done, 0, sizeof(int32_t), c->stream));
+    for (;;) {
+        rc = replay(c, true);
+        if (rc) break;
+        rc = sync_scalars(c);
+        if (rc) break;
+        if (c->h_sc->done) break;
+    }
+    int rc2 = upload_scalar(c, &c->d_sc->t_stop, INFINITY);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    if (steps_out) *steps_out = c->h_sc->steps - steps0;
+    return HG_OK;
+}
+
+int hg_energy(hg_ctx *c, double *kinetic, double *potential)
+{
+    if (!c) return HG_EINVAL;
+    int rc = sync_scalars(c);
+    if (rc) return rc;
+    const double t = c->h_sc->t_cur;
+    c->kernels += 4;
+    HG_CUDA(c, launch_energy(c->opts.energy_precision == HG_MIXED, c->st, c->n, t, c->eps * c->eps, c->xe, c->ve,
+                             c->phi_part, c->e_splits, c->e_part, c->e_g2, c->e_out, c->stream));
+    HG_CUDA(c, cudaMemcpyAsync(c->h_stage, c->e_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    HG_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (kinetic) *kinetic = c->h_stage[0];
+    if (potential) *potential = c->h_stage[1];
+    return HG_OK;
+}
+
+int hg_get_state(hg_ctx *c, hg_state *o)
+{
+    if (!c || !o) return HG_EINVAL;
+    const int64_t n = c->n;
+    struct F {
+        double *dst;
+        const double *src;
+        int64_t len;
+    } f[] = {{o->mass, c->st.mass, n}, {o->pos, c->st.x, 3 * n},  {o->vel, c->st.v, 3 * n},
+             {o->acc, c->st.a, 3 * n}, {o->jerk, c->st.j, 3 * n}, {o->snap, c->st.s, 3 * n},
+             {o->crackle, c->st.c, 3 * n}, {o->t, c->st.t, n},    {o->dt, c->st.dt, n}};
+    for (auto &q : f)
+        if (q.dst) HG_CUDA(c, cudaMemcpyAsync(q.dst, q.src, q.len * sizeof(double), cudaMemcpyDefault, c->stream));
+    int rc = sync_scalars(c);
+    if (rc) return rc;
+    o->t_sys = c->h_sc->t_cur;
+    return HG_OK;
+}
+
+int hg_set_state(hg_ctx *c, const hg_state *in)
+{
+    if (!c || !in) return HG_EINVAL;
+    if (!in->mass || !in->pos || !in->vel || !in->acc || !in->jerk || !in->snap || !in->crackle || !in->t || !in->dt)
+        return fail(c, HG_EINVAL, "every state field is required");
+    if (!isfinite(in->t_sys)) return fail(c, HG_EINVAL, "t_sys must be finite");
+    const int64_t n = c->n;
+    struct F {
+        double *dst;
+        const double *src;
+        int64_t len;
+    } f[] = {{c->st2.mass, in->mass, n}, {c->st2.x, in->pos, 3 * n},  {c->st2.v, in->vel, 3 * n},
+             {c->st2.a, in->acc, 3 * n}, {c->st2.j, in->jerk, 3 * n}, {c->st2.s, in->snap, 3 * n},
+             {c->st2.c, in->crackle, 3 * n}, {c->st2.t, in->t, n},    {c->st2.dt, in->dt, n}};
+    for (auto &q : f) HG_CUDA(c, cudaMemcpyAsync(q.dst, q.src, q.len * sizeof(double), cudaMemcpyDefault, c->stream));
+    int32_t flag = 0;
+    int rc = device_check(
+        c,
+        [&](int32_t *fl) {
+            return launch_validate_state(c->st2, n, c->opts.dt_min, c->opts.dt_max, fl, c->stream);
+        },
+        &flag);
+    if (rc) return rc;
+    if (flag)
+        return fail(c, HG_EINVAL,
+                    "state check failed: masses > 0, finite values, dt a power of two in [dt_min, dt_max], t a "
+                    "multiple of dt");
+    // Copy into the live arrays (captured graphs keep their pointers).
+    const State &d = c->st, &s = c->st2;
+    struct G {
+        double *dst;
+        const double *src;
+        int64_t len;
+    } g[] = {{d.mass, s.mass, n}, {d.x, s.x, 3 * n}, {d.v, s.v, 3 * n}, {d.a, s.a, 3 * n}, {d.j, s.j, 3 * n},
+             {d.s, s.s, 3 * n},   {d.c, s.c, 3 * n}, {d.t, s.t, n},     {d.dt, s.dt, n}};
+    for (auto &q : g)
+        HG_CUDA(c, cudaMemcpyAsync(q.dst, q.src, q.len * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    rc = upload_scalar(c, &c->d_sc->t_cur, in->t_sys);
+    if (rc) return rc;
+    invalidate(c);
+    return HG_OK;
+}
+
+int hg_get_stats(hg_ctx *c, hg_stats *o)
+{
+    if (!c || !o) return HG_EINVAL;
+    int rc = sync_scalars(c);
+    if (rc) return rc;
+    o->block_steps = c->h_sc->steps;
+    o->interactions = c->h_sc->interactions;
+    o->last_m = c->h_sc->m;
+    o->t_sys = c->h_sc->t_cur;
+    o->kernels = c->kernels;
+    return HG_OK;
+}
+
+int hg_get_profile(hg_ctx *c, hg_profile *o, int reset)
+{
+    if (!c || !o) return HG_EINVAL;
+    for (int q = 0; q < 5; ++q) o->ms[q] = c->prof_ms[q];
+    o->block_steps = c->prof_steps;
+    if (reset) {
+        for (int q = 0; q < 5; ++q) c->prof_ms[q] = 0.0;
+        c->prof_steps = 0;
+    }
+    return HG_OK;
+}
+
+int64_t hg_size(const hg_ctx *c) { return c ? c->n : 0; }
+
+const char *hg_last_error(const hg_ctx *c) { return c ? c->err.c_str() : ""; }
+
+void hg_free(hg_ctx *c) { release(c); }
+
+}  // extern "C"

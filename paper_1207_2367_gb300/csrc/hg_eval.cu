@@ -1,0 +1,483 @@
+// hg_eval.cu -- evaluation step (Sect. 3 item 2): acceleration, jerk and snap
+// of the active i-particles against all predicted j-particles, on CUDA cores
+// (the pair law is not a dense contraction), and the j-split reduction
+// (Table 1, section 4).
+//
+// One persistent kernel per precision.  A CTA of 128 threads walks work items
+// (i-tile, j-chunk).  j-records stream through a 3-stage ring of shared-memory
+// tiles filled by 1-D bulk (TMA) copies completing on mbarriers; tpi threads
+// share an i-particle and stride through each tile, then combine with warp
+// shuffles (and shared memory for tpi > 32).  Partial sums of each j-chunk go
+// to a [b][m][9] buffer that the reduction kernel sums in chunk order, so
+// results do not depend on scheduling.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hg_internal.cuh"
+
+namespace hg {
+namespace {
+
+constexpr int kFold = 32;   // FP32 pair sums are folded into the compensated sum every kFold j's
+
+// ------------------------------------------------------------------------
+// Mixed precision: FP32 pair arithmetic, double-single position differences,
+// Kahan-compensated FP32 sums (Sect. 5.7 hybrid precision, redesigned).
+// ------------------------------------------------------------------------
+struct Mixed {
+    static constexpr int TJ = kTJMixed;
+    static constexpr int I = kIMixed;
+    static constexpr int kMinBlocks = 4;
+    static constexpr uint32_t kStageBytes = TJ * 52;
+    struct IData {
+        float xh, yh, zh, xl, yl, zl, vx, vy, vz, ax, ay, az;
+    };
+    struct Acc {
+        float hi[I][9], lo[I][9];
+    };
+    typedef float Eps;
+
+    __device__ static void load_i(const Records &rec, int i, IData &d)
+    {
+        const float4 p0 = __ldg(static_cast<const float4 *>(rec.p[0]) + i);
+        const float4 p1 = __ldg(static_cast<const float4 *>(rec.p[1]) + i);
+        const float4 p2 = __ldg(static_cast<const float4 *>(rec.p[2]) + i);
+        const float p3 = __ldg(static_cast<const float *>(rec.p[3]) + i);
+        d.xh = p0.x; d.yh = p0.y; d.zh = p0.z;
+        d.xl = p1.x; d.yl = p1.y; d.zl = p1.z; d.ax = p1.w;
+        d.vx = p2.x; d.vy = p2.y; d.vz = p2.z; d.ay = p2.w;
+        d.az = p3;
+    }
+
+    __device__ static void zero(Acc &a)
+    {
+#pragma unroll
+        for (int k = 0; k < I; ++k)
+#pragma unroll
+            for (int c = 0; c < 9; ++c) a.hi[k][c] = a.lo[k][c] = 0.f;
+    }
+
+    __device__ static void issue(const Records &rec, int64_t tile, unsigned char *dst, uint64_t *bar)
+    {
+        const int64_t j0 = tile * TJ;
+        mbar_arrive_expect_tx(bar, kStageBytes);
+        bulk_g2s(dst, static_cast<const float4 *>(rec.p[0]) + j0, TJ * 16, bar);
+        bulk_g2s(dst + TJ * 16, static_cast<const float4 *>(rec.p[1]) + j0, TJ * 16, bar);
+        bulk_g2s(dst + TJ * 32, static_cast<const float4 *>(rec.p[2]) + j0, TJ * 16, bar);
+        bulk_g2s(dst + TJ * 48, static_cast<const float *>(rec.p[3]) + j0, TJ * 4, bar);
+    }
+
+    // One pair: r_ij = r_j - r_i from (hi, lo) parts, v_ij, a_ij, softened r^2,
+    // alpha r^2 = r.v, beta r^2 = v^2 + r.a + alpha^2 r^2, and
+    // A = m r / r^3, J = m v / r^3 - 3 alpha A, S = m a / r^3 - 6 alpha J - 3 beta A.
+    template <bool GUARD>
+    __device__ __forceinline__ static void pair(const IData &d, const float4 p0, const float4 p1,
+                                                const float4 p2, const float az, const float eps2,
+                                                float (&s)[9])
+    {
+        const float dx = (p0.x - d.xh) + (p1.x - d.xl);
+        const float dy = (p0.y - d.yh) + (p1.y - d.yl);
+        const float dz = (p0.z - d.zh) + (p1.z - d.zl);
+        const float dvx = p2.x - d.vx, dvy = p2.y - d.vy, dvz = p2.z - d.vz;
+        const float dax = p1.w - d.ax, day = p2.w - d.ay, daz = az - d.az;
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+        float rinv = rsqrt_approx(r2);
+        // One Newton-Raphson step for 1/sqrt(r2): y <- y + y/2 (1 - r2 y^2).
+        rinv = fmaf(0.5f * rinv, fmaf(-r2 * rinv, rinv, 1.f), rinv);
+        if (GUARD) rinv = (r2 > 0.f) ? rinv : 0.f;
+        const float rinv2 = rinv * rinv;
+        const float mr3 = p0.w * rinv * rinv2;
+        const float rv = fmaf(dz, dvz, fmaf(dy, dvy, dx * dvx));
+        const float v2ra =
+            fmaf(dz, daz, fmaf(dy, day, fmaf(dx, dax, fmaf(dvz, dvz, fmaf(dvy, dvy, dvx * dvx)))));
+        const float alpha = rv * rinv2;
+        const float beta = fmaf(alpha, alpha, v2ra * rinv2);
+        const float Ax = mr3 * dx, Ay = mr3 * dy, Az = mr3 * dz;
+        const float a3 = -3.f * alpha;
+        const float Jx = fmaf(a3, Ax, mr3 * dvx);
+        const float Jy = fmaf(a3, Ay, mr3 * dvy);
+        const float Jz = fmaf(a3, Az, mr3 * dvz);
+        const float a6 = -6.f * alpha, b3 = -3.f * beta;
+        s[0] += Ax;
+        s[1] += Ay;
+        s[2] += Az;
+        s[3] += Jx;
+        s[4] += Jy;
+        s[5] += Jz;
+        s[6] += fmaf(b3, Ax, fmaf(a6, Jx, mr3 * dax));
+        s[7] += fmaf(b3, Ay, fmaf(a6, Jy, mr3 * day));
+        s[8] += fmaf(b3, Az, fmaf(a6, Jz, mr3 * daz));
+    }
+
+    // Kahan step: hi + x with the running compensation lo (true sum = hi - lo).
+    __device__ __forceinline__ static void kahan(float &hi, float &lo, float x)
+    {
+        const float y = x - lo;
+        const float t = hi + y;
+        lo = (t - hi) - y;
+        hi = t;
+    }
+
+    template <bool GUARD>
+    __device__ static void tile(const unsigned char *sb, int tpi, int lane_j, const IData (&iv)[I], Acc &acc,
+                                Eps eps2)
+    {
+        const float4 *r0 = reinterpret_cast<const float4 *>(sb);
+        const float4 *r1 = r0 + TJ;
+        const float4 *r2 = r1 + TJ;
+        const float *r3 = reinterpret_cast<const float *>(r2 + TJ);
+        const int jpt = TJ / tpi;
+        const int fold = jpt < kFold ? jpt : kFold;
+        for (int g = 0; g < jpt; g += fold) {
+            float ch[I][9];
+#pragma unroll
+            for (int k = 0; k < I; ++k)
+#pragma unroll
+                for (int c = 0; c < 9; ++c) ch[k][c] = 0.f;
+#pragma unroll 2
+            for (int u = 0; u < fold; ++u) {
+                const int jj = (g + u) * tpi + lane_j;
+                const float4 p0 = r0[jj], p1 = r1[jj], p2 = r2[jj];
+                const float az = r3[jj];
+#pragma unroll
+                for (int k = 0; k < I; ++k) pair<GUARD>(iv[k], p0, p1, p2, az, eps2, ch[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < I; ++k)
+#pragma unroll
+                for (int c = 0; c < 9; ++c) kahan(acc.hi[k][c], acc.lo[k][c], ch[k][c]);
+        }
+    }
+
+    __device__ static void finish(const Acc &a, double (&out)[I][9])
+    {
+#pragma unroll
+        for (int k = 0; k < I; ++k)
+#pragma unroll
+            for (int c = 0; c < 9; ++c) out[k][c] = (double)a.hi[k][c] - (double)a.lo[k][c];
+    }
+};
+
+// ------------------------------------------------------------------------
+// FP64 throughout.
+// ------------------------------------------------------------------------
+struct F64 {
+    static constexpr int TJ = kTJF64;
+    static constexpr int I = kIF64;
+    static constexpr int kMinBlocks = 2;
+    static constexpr uint32_t kStageBytes = TJ * 80;
+    struct IData {
+        double x, y, z, vx, vy, vz, ax, ay, az;
+    };
+    struct Acc {
+        double s[I][9];
+    };
+    typedef double Eps;
+
+    __device__ static void load_i(const Records &rec, int i, IData &d)
+    {
+        const double2 q0 = __ldg(static_cast<const double2 *>(rec.p[0]) + i);
+        const double2 q1 = __ldg(static_cast<const double2 *>(rec.p[1]) + i);
+        const double2 q2 = __ldg(static_cast<const double2 *>(rec.p[2]) + i);
+        const double2 q3 = __ldg(static_cast<const double2 *>(rec.p[3]) + i);
+        const double2 q4 = __ldg(static_cast<const double2 *>(rec.p[4]) + i);
+        d.x = q0.x; d.y = q0.y; d.z = q1.x;
+        d.vx = q2.x; d.vy = q2.y; d.vz = q3.x;
+        d.ax = q3.y; d.ay = q4.x; d.az = q4.y;
+    }
+
+    __device__ static void zero(Acc &a)
+    {
+#pragma unroll
+        for (int k = 0; k < I; ++k)
+#pragma unroll
+            for (int c = 0; c < 9; ++c) a.s[k][c] = 0.0;
+    }
+
+    __device__ static void issue(const Records &rec, int64_t tile, unsigned char *dst, uint64_t *bar)
+    {
+        const int64_t j0 = tile * TJ;
+        mbar_arrive_expect_tx(bar, kStageBytes);
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+            bulk_g2s(dst + q * TJ * 16, static_cast<const double2 *>(rec.p[q]) + j0, TJ * 16, bar);
+    }
+
+    template <bool GUARD>
+    __device__ __forceinline__ static void pair(const IData &d, const double2 q0, const double2 q1,
+                                                const double2 q2, const double2 q3, const double2 q4,
+                                                const double eps2, double (&s)[9])
+    {
+        const double dx = q0.x - d.x, dy = q0.y - d.y, dz = q1.x - d.z;
+        const double dvx = q2.x - d.vx, dvy = q2.y - d.vy, dvz = q3.x - d.vz;
+        const double dax = q3.y - d.ax, day = q4.x - d.ay, daz = q4.y - d.az;
+        const double r2 = fma(dz, dz, fma(dy, dy, fma(dx, dx, eps2)));
+        double rinv = rsqrt(r2);
+        if (GUARD) rinv = (r2 > 0.0) ? rinv : 0.0;
+        const double rinv2 = rinv * rinv;
+        const double mr3 = q1.y * rinv * rinv2;
+        const double rv = fma(dz, dvz, fma(dy, dvy, dx * dvx));
+        const double v2ra = fma(dz, daz, fma(dy, day, fma(dx, dax, fma(dvz, dvz, fma(dvy, dvy, dvx * dvx)))));
+        const double alpha = rv * rinv2;
+        const double beta = fma(alpha, alpha, v2ra * rinv2);
+        const double Ax = mr3 * dx, Ay = mr3 * dy, Az = mr3 * dz;
+        const double a3 = -3.0 * alpha;
+        const double Jx = fma(a3, Ax, mr3 * dvx);
+        const double Jy = fma(a3, Ay, mr3 * dvy);
+        const double Jz = fma(a3, Az, mr3 * dvz);
+        const double a6 = -6.0 * alpha, b3 = -3.0 * beta;
+        s[0] += Ax;
+        s[1] += Ay;
+        s[2] += Az;
+        s[3] += Jx;
+        s[4] += Jy;
+        s[5] += Jz;
+        s[6] += fma(b3, Ax, fma(a6, Jx, mr3 * dax));
+        s[7] += fma(b3, Ay, fma(a6, Jy, mr3 * day));
+        s[8] += fma(b3, Az, fma(a6, Jz, mr3 * daz));
+    }
+
+    template <bool GUARD>
+    __device__ static void tile(const unsigned char *sb, int tpi, int lane_j, const IData (&iv)[I], Acc &acc,
+                                Eps eps2)
+    {
+        const double2 *q0 = reinterpret_cast<const double2 *>(sb);
+        const int jpt = TJ / tpi;
+#pragma unroll 2
+        for (int u = 0; u < jpt; ++u) {
+            const int jj = u * tpi + lane_j;
+            const double2 a = q0[jj], b = q0[TJ + jj], c = q0[2 * TJ + jj], d = q0[3 * TJ + jj],
+                          e = q0[4 * TJ + jj];
+#pragma unroll
+            for (int k = 0; k < I; ++k) pair<GUARD>(iv[k], a, b, c, d, e, eps2, acc.s[k]);
+        }
+    }
+
+    __device__ static void finish(const Acc &a, double (&out)[I][9])
+    {
+#pragma unroll
+        for (int k = 0; k < I; ++k)
+#pragma unroll
+            for (int c = 0; c < 9; ++c) out[k][c] = a.s[k][c];
+    }
+};
+
+template <class P>
+constexpr size_t smem_bytes()
+{
+    return (size_t)kStages * P::kStageBytes + kStages * sizeof(uint64_t) +
+           (kEvalThreads / 32) * P::I * 9 * sizeof(double);
+}
+
+template <class P, bool GUARD>
+__global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const EvalArgs args)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * P::kStageBytes);
+    double *red = reinterpret_cast<double *>(bars + kStages);
+    const int tid = threadIdx.x;
+
+    const int64_t m = args.m_dev ? *args.m_dev : args.m_host;
+    if (m <= 0) return;
+    const int64_t ntiles = args.npad / P::TJ;
+    const Plan pl = make_plan(m, ntiles, P::I, args.plan_grid, args.tpi_force, args.b_force, args.pcap);
+    if ((int64_t)blockIdx.x >= pl.n_items) return;
+
+    if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    const int tpi = pl.tpi;
+    const int lane_j = tid & (tpi - 1);
+    const int slot = tid / tpi;
+    const typename P::Eps eps2 = (typename P::Eps)args.eps2;
+    uint32_t seq = 0;   // tiles consumed so far by this CTA (mbarrier phase bookkeeping)
+
+    for (int64_t item = blockIdx.x; item < pl.n_items; item += gridDim.x) {
+        const int64_t itile = item / pl.b;
+        const int64_t split = item - itile * pl.b;
+        const int64_t tb = split * pl.tiles_per_split;
+        const int nt = (int)((ntiles - tb) < pl.tiles_per_split ? (ntiles - tb) : pl.tiles_per_split);
+
+        typename P::IData iv[P::I];
+        int64_t qi[P::I];
+#pragma unroll
+        for (int k = 0; k < P::I; ++k) {
+            qi[k] = itile * pl.ti + (int64_t)slot * P::I + k;
+            const int64_t qc = qi[k] < m ? qi[k] : m - 1;
+            P::load_i(args.rec, args.idx[qc], iv[k]);
+        }
+        typename P::Acc acc;
+        P::zero(acc);
+
+        if (tid == 0) {
+            const int pre = nt < kStages ? nt : kStages;
+            for (int s = 0; s < pre; ++s) {
+                const int st = (int)((seq + s) % kStages);
+                P::issue(args.rec, tb + s, smem + st * P::kStageBytes, &bars[st]);
+            }
+        }
+        for (int t = 0; t < nt; ++t) {
+            const uint32_t sq = seq + (uint32_t)t;
+            const int st = (int)(sq % kStages);
+            const bool ok = mbar_wait_bounded(&bars[st], (sq / kStages) & 1u, args.err);
+            if (ok) P::template tile<GUARD>(smem + st * P::kStageBytes, tpi, lane_j, iv, acc, eps2);
+            if (__syncthreads_or(!ok)) {
+                // A copy never completed: wait (bounded) for what is still in flight, then leave.
+                if (tid == 0) {
+                    const int issued = (t + kStages) < nt ? (t + kStages) : nt;
+                    for (int u = t; u < issued; ++u) {
+                        const uint32_t q = seq + (uint32_t)u;
+                        mbar_wait_bounded(&bars[q % kStages], (q / kStages) & 1u, args.err);
+                    }
+                }
+                return;
+            }
+            if (tid == 0 && t + kStages < nt) {
+                fence_proxy_async();
+                P::issue(args.rec, tb + t + kStages, smem + st * P::kStageBytes, &bars[st]);
+            }
+        }
+        seq += (uint32_t)nt;
+
+        double out[P::I][9];
+        P::finish(acc, out);
+        const int wspan = tpi < 32 ? tpi : 32;
+        for (int off = 1; off < wspan; off <<= 1) {
+#pragma unroll
+            for (int k = 0; k < P::I; ++k)
+#pragma unroll
+                for (int c = 0; c < 9; ++c) out[k][c] += __shfl_xor_sync(0xffffffffu, out[k][c], off);
+        }
+        if (tpi > 32) {
+            const int warp = tid >> 5, lane = tid & 31, wpg = tpi >> 5;
+            if (lane == 0) {
+#pragma unroll
+                for (int k = 0; k < P::I; ++k)
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) red[(warp * P::I + k) * 9 + c] = out[k][c];
+            }
+            __syncthreads();
+            if (lane == 0 && (warp % wpg) == 0) {
+#pragma unroll
+                for (int k = 0; k < P::I; ++k)
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) {
+                        double s = red[(warp * P::I + k) * 9 + c];
+                        for (int g = 1; g < wpg; ++g) s += red[((warp + g) * P::I + k) * 9 + c];
+                        out[k][c] = s;
+                    }
+            }
+            __syncthreads();
+        }
+        if (lane_j == 0) {
+#pragma unroll
+            for (int k = 0; k < P::I; ++k) {
+                if (qi[k] < m) {
+                    double *dst = args.partial + ((int64_t)split * m + qi[k]) * 9;
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) dst[c] = out[k][c];
+                }
+            }
+        }
+    }
+}
+
+// Table 1 section 4: sum the b j-chunk partials of every listed particle in
+// chunk order and scatter them to acc/jerk/snap [m][3].
+__global__ void k_reduce(const EvalArgs args, int tj, int ipt, double *ra, double *rj, double *rs)
+{
+    const int64_t m = args.m_dev ? *args.m_dev : args.m_host;
+    if (m <= 0) return;
+    const Plan pl = make_plan(m, args.npad / tj, ipt, args.plan_grid, args.tpi_force, args.b_force, args.pcap);
+    const int64_t total = m * 9;
+    if (pl.b <= 32) {
+        // Few chunks: one thread per (particle, component), chunks in order.
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+             e += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t q = e / 9;
+            const int c = (int)(e - q * 9);
+            double s = 0.0;
+            for (int sp = 0; sp < pl.b; ++sp) s += args.partial[((int64_t)sp * m + q) * 9 + c];
+            double *dst = c < 3 ? ra : (c < 6 ? rj : rs);
+            dst[q * 3 + (c % 3)] = s;
+        }
+    } else {
+        // Many chunks (small blocks): one warp per (particle, component); lane l
+        // sums chunks l, l+32, ..., then a fixed butterfly combines the lanes.
+        const int lane = threadIdx.x & 31;
+        const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+        const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        for (int64_t e = wid; e < total; e += nw) {
+            const int64_t q = e / 9;
+            const int c = (int)(e - q * 9);
+            double s = 0.0;
+            for (int sp = lane; sp < pl.b; sp += 32) s += args.partial[((int64_t)sp * m + q) * 9 + c];
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            if (lane == 0) {
+                double *dst = c < 3 ? ra : (c < 6 ? rj : rs);
+                dst[q * 3 + (c % 3)] = s;
+            }
+        }
+    }
+}
+
+template <class P, bool G>
+cudaError_t set_attr()
+{
+    return cudaFuncSetAttribute(k_eval<P, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<P>());
+}
+
+template <class P, bool G>
+int occupancy()
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_eval<P, G>, kEvalThreads, smem_bytes<P>()) !=
+        cudaSuccess)
+        return 1;
+    return nb > 0 ? nb : 1;
+}
+
+}  // namespace
+
+cudaError_t eval_setup(int)
+{
+    cudaError_t e;
+    if ((e = set_attr<Mixed, false>()) != cudaSuccess) return e;
+    if ((e = set_attr<Mixed, true>()) != cudaSuccess) return e;
+    if ((e = set_attr<F64, false>()) != cudaSuccess) return e;
+    return set_attr<F64, true>();
+}
+
+int eval_grid(bool mixed, int num_sms)
+{
+    return (mixed ? occupancy<Mixed, false>() : occupancy<F64, false>()) * num_sms;
+}
+
+cudaError_t launch_eval(bool mixed, const EvalArgs &args, int grid, cudaStream_t st)
+{
+    if (mixed) {
+        if (args.guard)
+            k_eval<Mixed, true><<<grid, kEvalThreads, smem_bytes<Mixed>(), st>>>(args);
+        else
+            k_eval<Mixed, false><<<grid, kEvalThreads, smem_bytes<Mixed>(), st>>>(args);
+    } else {
+        if (args.guard)
+            k_eval<F64, true><<<grid, kEvalThreads, smem_bytes<F64>(), st>>>(args);
+        else
+            k_eval<F64, false><<<grid, kEvalThreads, smem_bytes<F64>(), st>>>(args);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(bool mixed, const EvalArgs &args, int, double *ra, double *rj, double *rs,
+                          cudaStream_t st)
+{
+    k_reduce<<<1024, 256, 0, st>>>(args, mixed ? Mixed::TJ : F64::TJ, mixed ? Mixed::I : F64::I, ra, rj, rs);
+    return cudaGetLastError();
+}
+
+}  // namespace hg

@@ -1,0 +1,213 @@
+// hg_internal.cuh -- data layout, launch plans and PTX helpers shared by the
+// sm_103a kernels of the Hermite block-step engine.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hg.h"
+
+namespace hg {
+
+// ---------------------------------------------------------------------------
+// Device-side scalars of one context (one allocation).
+// ---------------------------------------------------------------------------
+struct DevScalars {
+    double t_cur;          // current block time (written by the next-block pass)
+    double t_stop;         // block steps whose time exceeds this are not taken
+    int64_t m;             // size of the current block
+    int64_t steps;         // block steps taken
+    int64_t interactions;  // sum of m * n over those steps
+    int32_t done;          // set when a next-block pass found t_next > t_stop
+    int32_t err;           // error bits (ERR_*)
+    int32_t flag;          // scratch result of validation kernels
+    int32_t pad;
+};
+
+enum : int32_t { ERR_TIMEOUT = 1, ERR_BADIDX = 2, ERR_STATE = 4, ERR_VALUE = 8 };
+
+// FP64 state of every particle at its own time, structure of arrays.
+struct State {
+    double *mass, *x, *v, *a, *j, *s, *c, *t, *dt;
+};
+
+// ---------------------------------------------------------------------------
+// Predicted j-records ("j-data") in structure-of-arrays form, npad entries
+// (npad a multiple of the j-tile).  Entries n..npad-1 are zero-mass padding
+// far away from every particle, so tiles never need a bounds check.
+//   mixed: r0 = float4(x_hi, y_hi, z_hi, m)     r1 = float4(x_lo, y_lo, z_lo, a_x)
+//          r2 = float4(v_x, v_y, v_z, a_y)      r3 = float(a_z)          52 B/particle
+//   fp64 : q0 = double2(x, y)  q1 = double2(z, m)  q2 = double2(v_x, v_y)
+//          q3 = double2(v_z, a_x)  q4 = double2(a_y, a_z)                   80 B/particle
+// ---------------------------------------------------------------------------
+struct Records {
+    void *p[5];
+};
+
+constexpr int kEvalThreads = 128;
+constexpr int kStages = 3;
+constexpr int kTJMixed = 256;   // j-records per shared-memory tile, mixed
+constexpr int kTJF64 = 128;     // j-records per shared-memory tile, fp64
+constexpr int kIMixed = 2;      // i-particles held per thread, mixed
+constexpr int kIF64 = 1;        // i-particles held per thread, fp64
+constexpr int kMaxTPI = 64;
+constexpr double kPadCoord = 1.0e18;
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+
+// ---------------------------------------------------------------------------
+// Work decomposition of one evaluation (Sect. 3 "Bfactor", redesigned): the m
+// active particles form i-tiles of ti = (threads / tpi) * i_per_thread; each
+// i-tile is split over b j-chunks of whole tiles ("j-split"), one work item
+// per (i-tile, j-chunk).  tpi threads share an i-particle when m is small, so
+// every lane has work; b spreads small blocks over all SMs.  A pure function
+// of its arguments: the evaluation and the reduction compute the same plan.
+// ---------------------------------------------------------------------------
+struct Plan {
+    int tpi, ti, b;
+    int64_t n_itiles, tiles_per_split, n_items;
+};
+
+__host__ __device__ inline Plan make_plan(int64_t m, int64_t ntiles, int i_per_thread, int grid,
+                                          int tpi_force, int b_force, int64_t pcap)
+{
+    Plan p;
+    int tpi = 1;
+    if (tpi_force > 0) {
+        tpi = tpi_force;
+    } else {
+        int64_t want = (int64_t)kEvalThreads * i_per_thread / (m > 0 ? m : 1);
+        while (tpi * 2 <= want && tpi < kMaxTPI) tpi *= 2;
+    }
+    p.tpi = tpi;
+    p.ti = kEvalThreads / tpi * i_per_thread;
+    p.n_itiles = (m + p.ti - 1) / p.ti;
+    int64_t b;
+    if (b_force > 0) {
+        b = b_force;
+    } else {
+        // Aim at >= 2 items per resident CTA; for large blocks pick the split
+        // (1..4) with the least wave quantization loss.
+        int64_t target = 2 * (int64_t)grid;
+        b = (target + p.n_itiles - 1) / p.n_itiles;
+        if (b <= 1) {
+            double best = -1.0;
+            b = 1;
+            for (int64_t c = 1; c <= 4; ++c) {
+                double items = (double)(p.n_itiles * c);
+                double waves = items / grid;
+                double eff = waves / (double)((int64_t)(waves + 0.999999999));
+                if (eff > best + 1e-3) { best = eff; b = c; }
+            }
+        }
+    }
+    int64_t mcap = m > 0 ? m : 1;
+    if (b * mcap > pcap) b = pcap / mcap;
+    if (b < 1) b = 1;
+    if (b > ntiles) b = ntiles;
+    p.tiles_per_split = (ntiles + b - 1) / b;
+    p.b = (int)((ntiles + p.tiles_per_split - 1) / p.tiles_per_split);   // no empty chunk
+    p.n_items = p.n_itiles * p.b;
+    return p;
+}
+
+struct EvalArgs {
+    Records rec;
+    int64_t npad;
+    const int32_t *idx;      // active list (device)
+    const int64_t *m_dev;    // block size on the device (graph mode), or nullptr
+    int64_t m_host;          // block size when m_dev == nullptr
+    double *partial;         // [b][m][9] partial sums
+    int64_t pcap;            // capacity of partial in units of 9 doubles
+    double eps2;
+    int guard;               // eps == 0: skip r^2 == 0 pairs
+    int tpi_force, b_force;
+    int plan_grid;           // grid size the plan is made for (launch grid may be smaller)
+    int32_t *err;
+};
+
+// Host-side launchers (hg_eval.cu).
+cudaError_t eval_setup(int device);
+int eval_grid(bool mixed, int num_sms);
+cudaError_t launch_eval(bool mixed, const EvalArgs &args, int grid, cudaStream_t st);
+// Sums the b partials of each listed particle into res_{a,j,s} [m][3].
+cudaError_t launch_reduce(bool mixed, const EvalArgs &args, int eval_grid, double *ra, double *rj,
+                          double *rs, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// PTX helpers: mbarrier and bulk (TMA) copies global -> shared.
+// ---------------------------------------------------------------------------
+#if defined(__CUDACC__)
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of bar, giving up after kWaitCycles (sets ERR_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int32_t *err)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    long long start = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - start > kWaitCycles) {
+            atomicOr(err, ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// 1-D bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
+// from global to this CTA's shared memory, completing on bar.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Hardware reciprocal square root (single MUFU instruction, flush-to-zero).
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+#endif
+
+}  // namespace hg

@@ -1,0 +1,622 @@
+// hg_kernels.cu -- the FP64 parts of a block step (next-block selection,
+// predictor, corrector with the time-step update), start-up, energy and
+// input validation.  Sect. 3 of the HiGPUs paper; Table 1 sections 1, 2, 8.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "hg_kernels.cuh"
+
+namespace hg {
+namespace {
+
+constexpr int kNBThreads = 1024;
+
+__device__ __forceinline__ double block_min(double v, double *sh)
+{
+    for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = (l < (int)(blockDim.x >> 5)) ? sh[l] : INFINITY;
+        for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off));
+        if (l == 0) sh[0] = v;
+    }
+    __syncthreads();
+    return sh[0];
+}
+
+__device__ __forceinline__ int64_t block_sum_i64(int64_t v, int64_t *sh)
+{
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0;
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (l == 0) sh[0] = v;
+    }
+    __syncthreads();
+    return sh[0];
+}
+
+// ------------------------------------------------------------------------
+// Table 1 section 1: next block time and the ascending list of due particles.
+// Three passes over t_i + dt_i (exact: all times are dyadic), one CTA per
+// contiguous chunk, no atomics: results do not depend on scheduling.
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(kNBThreads) k_nb_min(const double *t, const double *dt, int64_t n, int64_t chunk,
+                                                       double *part)
+{
+    __shared__ double sh[32];
+    const int64_t lo = blockIdx.x * chunk, hi = (lo + chunk < n) ? lo + chunk : n;
+    double v = INFINITY;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) v = fmin(v, t[i] + dt[i]);
+    v = block_min(v, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+__device__ __forceinline__ double global_min(const double *part, int g, double *sh)
+{
+    double v = INFINITY;
+    for (int c = threadIdx.x; c < g; c += blockDim.x) v = fmin(v, part[c]);
+    return block_min(v, sh);
+}
+
+__global__ void __launch_bounds__(kNBThreads) k_nb_count(const double *t, const double *dt, int64_t n, int64_t chunk,
+                                                         const double *part, int g, int32_t *cnt)
+{
+    __shared__ double sh[32];
+    __shared__ int64_t shi[32];
+    const double tn = global_min(part, g, sh);
+    const int64_t lo = blockIdx.x * chunk, hi = (lo + chunk < n) ? lo + chunk : n;
+    int64_t c = 0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) c += (t[i] + dt[i] == tn) ? 1 : 0;
+    c = block_sum_i64(c, shi);
+    if (threadIdx.x == 0) cnt[blockIdx.x] = (int32_t)c;
+}
+
+__global__ void __launch_bounds__(kNBThreads) k_nb_scatter(const double *t, const double *dt, int64_t n,
+                                                           int64_t chunk, const double *part, int g,
+                                                           const int32_t *cnt, int32_t *idx, DevScalars *sc,
+                                                           int count_step)
+{
+    __shared__ double sh[32];
+    __shared__ int64_t shi[32];
+    __shared__ int32_t woff[33];
+    const double tn = global_min(part, g, sh);
+    const double t_stop = sc->t_stop;
+    if (tn > t_stop) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            sc->m = 0;
+            sc->done = 1;
+        }
+        return;
+    }
+    int64_t pre = 0;
+    for (int c = threadIdx.x; c < (int)blockIdx.x; c += blockDim.x) pre += cnt[c];
+    pre = block_sum_i64(pre, shi);
+    if (blockIdx.x == 0) {
+        int64_t tot = 0;
+        for (int c = threadIdx.x; c < g; c += blockDim.x) tot += cnt[c];
+        tot = block_sum_i64(tot, shi);
+        if (threadIdx.x == 0) {
+            sc->m = tot;
+            sc->t_cur = tn;
+            sc->done = 0;
+            if (count_step) {
+                sc->steps += 1;
+                sc->interactions += tot * n;
+            }
+        }
+    }
+    const int64_t lo = blockIdx.x * chunk, hi = (lo + chunk < n) ? lo + chunk : n;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int64_t base = lo; base < hi; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool due = (i < hi) && (t[i] + dt[i] == tn);
+        const unsigned ball = __ballot_sync(0xffffffffu, due);
+        if (l == 0) woff[w] = __popc(ball);
+        __syncthreads();
+        if (w == 0) {
+            int v = (l < (int)(blockDim.x >> 5)) ? woff[l] : 0;
+            int incl = v;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, off);
+                if (l >= off) incl += u;
+            }
+            woff[l] = incl - v;
+            if (l == 31) woff[32] = incl;
+        }
+        __syncthreads();
+        if (due) idx[pre + woff[w] + __popc(ball & ((1u << l) - 1u))] = (int32_t)i;
+        pre += woff[32];
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------
+// Sect. 3 item 1: Taylor predictor through crackle, FP64, h = t - t_j.
+// ------------------------------------------------------------------------
+struct Pred {
+    double x[3], v[3], a[3];
+};
+
+__device__ __forceinline__ Pred predict_one(const State &st, int64_t i, double tt)
+{
+    Pred p;
+    const double h = tt - st.t[i];
+    const double h2 = h * h * 0.5;              // h^2/2
+    const double h3 = h2 * h * (1.0 / 3.0);     // h^3/6
+    const double h4 = h3 * h * 0.25;            // h^4/24
+    const double h5 = h4 * h * 0.2;             // h^5/120
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int64_t q = 3 * i + k;
+        const double x = st.x[q], v = st.v[q], a = st.a[q], j = st.j[q], s = st.s[q], c = st.c[q];
+        p.x[k] = x + fma(h, v, fma(h2, a, fma(h3, j, fma(h4, s, h5 * c))));
+        p.v[k] = v + fma(h, a, fma(h2, j, fma(h3, s, h4 * c)));
+        p.a[k] = a + fma(h, j, fma(h2, s, h3 * c));
+    }
+    return p;
+}
+
+template <bool MIXED>
+__global__ void k_predict(const State st, const Records rec, int64_t n, int64_t npad, const double *t_dev,
+                          double t_host, const int64_t *m_dev)
+{
+    if (m_dev && *m_dev <= 0) return;
+    const double tt = t_dev ? *t_dev : t_host;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npad; i += (int64_t)gridDim.x * blockDim.x) {
+        if (MIXED) {
+            float4 r0, r1, r2;
+            float r3;
+            if (i < n) {
+                const Pred p = predict_one(st, i, tt);
+                float hi[3], lo[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    hi[k] = __double2float_rn(p.x[k]);
+                    lo[k] = __double2float_rn(p.x[k] - (double)hi[k]);
+                }
+                r0 = make_float4(hi[0], hi[1], hi[2], __double2float_rn(st.mass[i]));
+                r1 = make_float4(lo[0], lo[1], lo[2], __double2float_rn(p.a[0]));
+                r2 = make_float4(__double2float_rn(p.v[0]), __double2float_rn(p.v[1]), __double2float_rn(p.v[2]),
+                                 __double2float_rn(p.a[1]));
+                r3 = __double2float_rn(p.a[2]);
+            } else {
+                const float far = (float)kPadCoord;
+                r0 = make_float4(far, far, far, 0.f);
+                r1 = make_float4(0.f, 0.f, 0.f, 0.f);
+                r2 = r1;
+                r3 = 0.f;
+            }
+            static_cast<float4 *>(rec.p[0])[i] = r0;
+            static_cast<float4 *>(rec.p[1])[i] = r1;
+            static_cast<float4 *>(rec.p[2])[i] = r2;
+            static_cast<float *>(rec.p[3])[i] = r3;
+        } else {
+            double2 q0, q1, q2, q3, q4;
+            if (i < n) {
+                const Pred p = predict_one(st, i, tt);
+                q0 = make_double2(p.x[0], p.x[1]);
+                q1 = make_double2(p.x[2], st.mass[i]);
+                q2 = make_double2(p.v[0], p.v[1]);
+                q3 = make_double2(p.v[2], p.a[0]);
+                q4 = make_double2(p.a[1], p.a[2]);
+            } else {
+                q0 = make_double2(kPadCoord, kPadCoord);
+                q1 = make_double2(kPadCoord, 0.0);
+                q2 = q3 = q4 = make_double2(0.0, 0.0);
+            }
+            static_cast<double2 *>(rec.p[0])[i] = q0;
+            static_cast<double2 *>(rec.p[1])[i] = q1;
+            static_cast<double2 *>(rec.p[2])[i] = q2;
+            static_cast<double2 *>(rec.p[3])[i] = q3;
+            static_cast<double2 *>(rec.p[4])[i] = q4;
+        }
+    }
+}
+
+// Predicted FP64 positions and velocities (energy diagnostics).
+__global__ void k_predict_xv(const State st, int64_t n, double tt, double *xe, double *ve)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const Pred p = predict_one(st, i, tt);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            xe[3 * i + k] = p.x[k];
+            ve[3 * i + k] = p.v[k];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// Time steps: generalized Aarseth criterion and power-of-two blocks.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ double norm3(const double *p)
+{
+    return sqrt(__dadd_rn(__dadd_rn(__dmul_rn(p[0], p[0]), __dmul_rn(p[1], p[1])), __dmul_rn(p[2], p[2])));
+}
+
+// eta (A^(1)/A^(p-2))^(1/(p-3)) with A^(s) = sqrt(|a^(s-1)||a^(s+1)| + |a^(s)|^2);
+// d holds a^(0..p-1) (p = 4 or 6).
+__device__ double criterion(double eta, int p, const double (*d)[3])
+{
+    double nr[6];
+    for (int s = 0; s < p; ++s) nr[s] = norm3(d[s]);
+    const double A1 = sqrt(__dadd_rn(__dmul_rn(nr[0], nr[2]), __dmul_rn(nr[1], nr[1])));
+    const double Ap = sqrt(__dadd_rn(__dmul_rn(nr[p - 3], nr[p - 1]), __dmul_rn(nr[p - 2], nr[p - 2])));
+    if (Ap == 0.0) return INFINITY;
+    const double ratio = A1 / Ap;
+    return (p == 4) ? eta * ratio : eta * cbrt(ratio);
+}
+
+// Shrink to the largest 2^k <= crit; grow x2 only when t_new is a multiple of
+// the doubled step; clamp to [dt_min, dt_max].
+__device__ double block_dt(double crit, double dt, double t_new, double dt_min, double dt_max)
+{
+    if (crit < dt) {
+        while (dt > crit && dt > dt_min) dt *= 0.5;
+    } else if (crit >= 2.0 * dt && 2.0 * dt <= dt_max && fmod(t_new, 2.0 * dt) == 0.0) {
+        dt *= 2.0;
+    }
+    return fmin(fmax(dt, dt_min), dt_max);
+}
+
+__device__ double block_dt_init(double crit, double dt_min, double dt_max)
+{
+    double dt = dt_max;
+    while (dt > crit && dt > dt_min) dt *= 0.5;
+    return dt;
+}
+
+// Start-up: store a, jerk, snap of the full evaluation, crackle = 0, t = 0 and
+// the first step from the p = 4 criterion with eta_init.
+__global__ void k_start(State st, int64_t n, const double *ra, const double *rj, const double *rs, StepParams sp)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double d[4][3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            d[0][k] = ra[3 * i + k];
+            d[1][k] = rj[3 * i + k];
+            d[2][k] = rs[3 * i + k];
+            d[3][k] = 0.0;
+            st.a[3 * i + k] = d[0][k];
+            st.j[3 * i + k] = d[1][k];
+            st.s[3 * i + k] = d[2][k];
+            st.c[3 * i + k] = 0.0;
+        }
+        st.t[i] = 0.0;
+        st.dt[i] = block_dt_init(criterion(sp.eta_init, 4, d), sp.dt_min, sp.dt_max);
+    }
+}
+
+// ------------------------------------------------------------------------
+// Sect. 3 item 3: corrector, Hermite interpolation for crackle/pop/a^(5),
+// p = 6 criterion and the new block step, for the m particles of the block.
+// ------------------------------------------------------------------------
+__global__ void k_correct(State st, const int32_t *idx, const int64_t *m_dev, int64_t m_host, const double *ra,
+                          const double *rj, const double *rs, StepParams sp)
+{
+    const int64_t m = m_dev ? *m_dev : m_host;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx[q];
+        const double h = st.dt[i];
+        const double t1 = st.t[i] + h;
+        const double hh = h / 2.0, h2 = h * h / 10.0, h3 = h * h * h / 120.0;
+        double d[6][3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double x0 = st.x[3 * i + k], v0 = st.v[3 * i + k], a0 = st.a[3 * i + k];
+            const double j0 = st.j[3 * i + k], s0 = st.s[3 * i + k];
+            const double a1 = ra[3 * q + k], j1 = rj[3 * q + k], s1 = rs[3 * q + k];
+            const double v1 = v0 + hh * (a1 + a0) - h2 * (j1 - j0) + h3 * (s1 + s0);
+            const double x1 = x0 + hh * (v1 + v0) - h2 * (a1 - a0) + h3 * (j1 + j0);
+            // Degree-5 interpolant through a, jerk, snap at both ends.
+            const double A = a1 - a0 - j0 * h - s0 * h * h / 2.0;
+            const double J = (j1 - j0 - s0 * h) * h;
+            const double S = (s1 - s0) * h * h;
+            d[0][k] = a1;
+            d[1][k] = j1;
+            d[2][k] = s1;
+            d[3][k] = (60.0 * A - 36.0 * J + 9.0 * S) / (h * h * h);
+            d[4][k] = (360.0 * A - 192.0 * J + 36.0 * S) / (h * h * h * h);
+            d[5][k] = (720.0 * A - 360.0 * J + 60.0 * S) / (h * h * h * h * h);
+            st.x[3 * i + k] = x1;
+            st.v[3 * i + k] = v1;
+            st.a[3 * i + k] = a1;
+            st.j[3 * i + k] = j1;
+            st.s[3 * i + k] = s1;
+            st.c[3 * i + k] = d[3][k];
+        }
+        st.t[i] = t1;
+        st.dt[i] = block_dt(criterion(sp.eta, 6, d), h, t1, sp.dt_min, sp.dt_max);
+    }
+}
+
+// ------------------------------------------------------------------------
+// Energy: Sect. 2 softened potential, W = -1/2 sum_i m_i sum_{j != i} m_j /
+// sqrt(r^2 + eps^2), kinetic 1/2 sum m v^2.  Per-i potentials over j-chunks,
+// then ordered sums.
+// ------------------------------------------------------------------------
+constexpr int kPotThreads = 128;
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kPotThreads) k_potential(const double *xe, const double *mass, int64_t n,
+                                                            int64_t jchunk, double eps2, double *phi_part)
+{
+    __shared__ double sx[kPotThreads], sy[kPotThreads], sz[kPotThreads], sm[kPotThreads];
+    __shared__ float fh[3][kPotThreads], fl[3][kPotThreads], fm[kPotThreads];
+    const int64_t i = blockIdx.x * (int64_t)kPotThreads + threadIdx.x;
+    const int64_t ic = i < n ? i : n - 1;
+    const int64_t j0 = blockIdx.y * jchunk;
+    const int64_t j1 = (j0 + jchunk < n) ? j0 + jchunk : n;
+    double xi[3] = {xe[3 * ic], xe[3 * ic + 1], xe[3 * ic + 2]};
+    float xih[3], xil[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        xih[k] = __double2float_rn(xi[k]);
+        xil[k] = __double2float_rn(xi[k] - (double)xih[k]);
+    }
+    double phi = 0.0;
+    float hi = 0.f, lo = 0.f;
+    const float eps2f = (float)eps2;
+    for (int64_t jb = j0; jb < j1; jb += kPotThreads) {
+        const int64_t j = jb + threadIdx.x;
+        __syncthreads();
+        if (j < j1) {
+            if (MIXED) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const double x = xe[3 * j + k];
+                    fh[k][threadIdx.x] = __double2float_rn(x);
+                    fl[k][threadIdx.x] = __double2float_rn(x - (double)fh[k][threadIdx.x]);
+                }
+                fm[threadIdx.x] = __double2float_rn(mass[j]);
+            } else {
+                sx[threadIdx.x] = xe[3 * j];
+                sy[threadIdx.x] = xe[3 * j + 1];
+                sz[threadIdx.x] = xe[3 * j + 2];
+                sm[threadIdx.x] = mass[j];
+            }
+        }
+        __syncthreads();
+        const int cnt = (int)((j1 - jb) < kPotThreads ? (j1 - jb) : kPotThreads);
+        if (MIXED) {
+            float ch = 0.f;
+            for (int u = 0; u < cnt; ++u) {
+                const float dx = (fh[0][u] - xih[0]) + (fl[0][u] - xil[0]);
+                const float dy = (fh[1][u] - xih[1]) + (fl[1][u] - xil[1]);
+                const float dz = (fh[2][u] - xih[2]) + (fl[2][u] - xil[2]);
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2f)));
+                float r = rsqrt_approx(r2);
+                r = r * fmaf(-0.5f * r2, r * r, 1.5f);           // one Newton step
+                ch += (jb + u == i) ? 0.f : fm[u] * r;
+            }
+            const float y = ch - lo;
+            const float tt = hi + y;
+            lo = (tt - hi) - y;
+            hi = tt;
+        } else {
+            for (int u = 0; u < cnt; ++u) {
+                const double dx = sx[u] - xi[0], dy = sy[u] - xi[1], dz = sz[u] - xi[2];
+                const double r2 = fma(dz, dz, fma(dy, dy, fma(dx, dx, eps2)));
+                phi += (jb + u == i) ? 0.0 : sm[u] * rsqrt(r2);
+            }
+        }
+    }
+    if (MIXED) phi = (double)hi - (double)lo;
+    if (i < n) phi_part[blockIdx.y * n + i] = phi;
+}
+
+__global__ void k_energy_sum(const double *mass, const double *ve, const double *phi_part, int64_t n, int nsplit,
+                             double *part2)
+{
+    __shared__ double shk[32], shw[32];
+    double k = 0.0, w = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double phi = 0.0;
+        for (int s = 0; s < nsplit; ++s) phi += phi_part[s * n + i];
+        const double vx = ve[3 * i], vy = ve[3 * i + 1], vz = ve[3 * i + 2];
+        k += 0.5 * mass[i] * (vx * vx + vy * vy + vz * vz);
+        w += mass[i] * phi;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        k += __shfl_xor_sync(0xffffffffu, k, off);
+        w += __shfl_xor_sync(0xffffffffu, w, off);
+    }
+    const int wp = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        shk[wp] = k;
+        shw[wp] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sk = 0.0, sw = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+            sk += shk[q];
+            sw += shw[q];
+        }
+        part2[2 * blockIdx.x] = sk;
+        part2[2 * blockIdx.x + 1] = sw;
+    }
+}
+
+__global__ void k_energy_final(const double *part2, int g, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double k = 0.0, w = 0.0;
+        for (int c = 0; c < g; ++c) {
+            k += part2[2 * c];
+            w += part2[2 * c + 1];
+        }
+        out[0] = k;
+        out[1] = -0.5 * w;
+    }
+}
+
+// ------------------------------------------------------------------------
+// Validation (flags, never traps).
+// ------------------------------------------------------------------------
+__device__ __forceinline__ bool is_pow2(double x)
+{
+    int e;
+    return x > 0.0 && isfinite(x) && frexp(x, &e) == 0.5;
+}
+
+__global__ void k_validate_init(const double *mass, const double *x, const double *v, int64_t n, int32_t *flag)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        bool ok = isfinite(mass[i]) && mass[i] > 0.0;
+        for (int k = 0; k < 3; ++k) ok = ok && isfinite(x[3 * i + k]) && isfinite(v[3 * i + k]);
+        if (!ok) atomicOr(flag, ERR_VALUE);
+    }
+}
+
+__global__ void k_validate_state(const State st, int64_t n, double dt_min, double dt_max, int32_t *flag)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        bool ok = isfinite(st.mass[i]) && st.mass[i] > 0.0 && isfinite(st.t[i]);
+        for (int k = 0; k < 3; ++k) {
+            const int64_t q = 3 * i + k;
+            ok = ok && isfinite(st.x[q]) && isfinite(st.v[q]) && isfinite(st.a[q]) && isfinite(st.j[q]) &&
+                 isfinite(st.s[q]) && isfinite(st.c[q]);
+        }
+        const double dt = st.dt[i];
+        ok = ok && is_pow2(dt) && dt >= dt_min && dt <= dt_max && fmod(st.t[i], dt) == 0.0;
+        if (!ok) atomicOr(flag, ERR_VALUE);
+    }
+}
+
+__global__ void k_validate_idx(const int32_t *idx, int64_t m, int64_t n, int32_t *flag)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m; q += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = idx[q];
+        bool ok = i >= 0 && (int64_t)i < n;
+        if (q > 0) ok = ok && idx[q - 1] < i;
+        if (!ok) atomicOr(flag, ERR_BADIDX);
+    }
+}
+
+// hg_correct preconditions: same list as the evaluation (when given) and every
+// listed particle due exactly at the prediction time.
+__global__ void k_check_correct(const State st, const int32_t *given, const int32_t *cur, int64_t m, double t_pred,
+                                int32_t *flag)
+{
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m; q += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = cur[q];
+        bool ok = (given == nullptr) || (given[q] == i);
+        ok = ok && (st.t[i] + st.dt[i] == t_pred);
+        if (!ok) atomicOr(flag, ERR_STATE);
+    }
+}
+
+inline int grid_for(int64_t work, int threads, int cap)
+{
+    int64_t g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    return (int)(g < cap ? g : cap);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host launchers.
+// ---------------------------------------------------------------------------
+int nb_grid(int64_t n) { return (int)((n + kNBChunk - 1) / kNBChunk); }
+
+cudaError_t launch_next_block(const State &st, int64_t n, double *part, int32_t *cnt, int32_t *idx, DevScalars *sc,
+                              int count_step, cudaStream_t s)
+{
+    const int g = nb_grid(n);
+    k_nb_min<<<g, kNBThreads, 0, s>>>(st.t, st.dt, n, kNBChunk, part);
+    k_nb_count<<<g, kNBThreads, 0, s>>>(st.t, st.dt, n, kNBChunk, part, g, cnt);
+    k_nb_scatter<<<g, kNBThreads, 0, s>>>(st.t, st.dt, n, kNBChunk, part, g, cnt, idx, sc, count_step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_predict(bool mixed, const State &st, const Records &rec, int64_t n, int64_t npad,
+                           const double *t_dev, double t_host, const int64_t *m_dev, cudaStream_t s)
+{
+    const int g = grid_for(npad, 256, 1 << 20);
+    if (mixed)
+        k_predict<true><<<g, 256, 0, s>>>(st, rec, n, npad, t_dev, t_host, m_dev);
+    else
+        k_predict<false><<<g, 256, 0, s>>>(st, rec, n, npad, t_dev, t_host, m_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_start(const State &st, int64_t n, const double *ra, const double *rj, const double *rs,
+                         const StepParams &sp, cudaStream_t s)
+{
+    k_start<<<grid_for(n, 256, 1 << 20), 256, 0, s>>>(st, n, ra, rj, rs, sp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_correct(const State &st, const int32_t *idx, const int64_t *m_dev, int64_t m_host, int64_t n_max,
+                           const double *ra, const double *rj, const double *rs, const StepParams &sp, cudaStream_t s)
+{
+    k_correct<<<grid_for(n_max, 128, 4096), 128, 0, s>>>(st, idx, m_dev, m_host, ra, rj, rs, sp);
+    return cudaGetLastError();
+}
+
+int energy_splits(int64_t n, int num_sms)
+{
+    const int64_t itiles = (n + kPotThreads - 1) / kPotThreads;
+    int64_t b = (4 * (int64_t)num_sms + itiles - 1) / itiles;
+    const int64_t jt = (n + kPotThreads - 1) / kPotThreads;
+    if (b > jt) b = jt;
+    if (b > 64) b = 64;
+    return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_energy(bool mixed, const State &st, int64_t n, double t, double eps2, double *xe, double *ve,
+                          double *phi_part, int nsplit, double *part2, int g2, double *out2, cudaStream_t s)
+{
+    k_predict_xv<<<grid_for(n, 256, 1 << 20), 256, 0, s>>>(st, n, t, xe, ve);
+    int64_t jchunk = (n + nsplit - 1) / nsplit;
+    jchunk = (jchunk + kPotThreads - 1) / kPotThreads * kPotThreads;
+    dim3 grid((unsigned)((n + kPotThreads - 1) / kPotThreads), (unsigned)nsplit);
+    if (mixed)
+        k_potential<true><<<grid, kPotThreads, 0, s>>>(xe, st.mass, n, jchunk, eps2, phi_part);
+    else
+        k_potential<false><<<grid, kPotThreads, 0, s>>>(xe, st.mass, n, jchunk, eps2, phi_part);
+    k_energy_sum<<<g2, 256, 0, s>>>(st.mass, ve, phi_part, n, nsplit, part2);
+    k_energy_final<<<1, 32, 0, s>>>(part2, g2, out2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate_init(const double *mass, const double *x, const double *v, int64_t n, int32_t *flag,
+                                 cudaStream_t s)
+{
+    k_validate_init<<<grid_for(n, 256, 4096), 256, 0, s>>>(mass, x, v, n, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate_state(const State &st, int64_t n, double dt_min, double dt_max, int32_t *flag,
+                                  cudaStream_t s)
+{
+    k_validate_state<<<grid_for(n, 256, 4096), 256, 0, s>>>(st, n, dt_min, dt_max, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate_idx(const int32_t *idx, int64_t m, int64_t n, int32_t *flag, cudaStream_t s)
+{
+    k_validate_idx<<<grid_for(m, 256, 4096), 256, 0, s>>>(idx, m, n, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_correct(const State &st, const int32_t *given, const int32_t *cur, int64_t m, double t_pred,
+                                 int32_t *flag, cudaStream_t s)
+{
+    k_check_correct<<<grid_for(m, 256, 4096), 256, 0, s>>>(st, given, cur, m, t_pred, flag);
+    return cudaGetLastError();
+}
+
+}  // namespace hg

@@ -1,0 +1,34 @@
+// hg_kernels.cuh -- launchers of the FP64 block-step kernels (hg_kernels.cu).
+#pragma once
+
+#include "hg_internal.cuh"
+
+namespace hg {
+
+struct StepParams {
+    double eta, eta_init, dt_min, dt_max;
+};
+
+constexpr int64_t kNBChunk = 8192;   // particles per CTA in the next-block passes
+
+int nb_grid(int64_t n);
+cudaError_t launch_next_block(const State &st, int64_t n, double *part, int32_t *cnt, int32_t *idx, DevScalars *sc,
+                              int count_step, cudaStream_t s);
+cudaError_t launch_predict(bool mixed, const State &st, const Records &rec, int64_t n, int64_t npad,
+                           const double *t_dev, double t_host, const int64_t *m_dev, cudaStream_t s);
+cudaError_t launch_start(const State &st, int64_t n, const double *ra, const double *rj, const double *rs,
+                         const StepParams &sp, cudaStream_t s);
+cudaError_t launch_correct(const State &st, const int32_t *idx, const int64_t *m_dev, int64_t m_host, int64_t n_max,
+                           const double *ra, const double *rj, const double *rs, const StepParams &sp, cudaStream_t s);
+int energy_splits(int64_t n, int num_sms);
+cudaError_t launch_energy(bool mixed, const State &st, int64_t n, double t, double eps2, double *xe, double *ve,
+                          double *phi_part, int nsplit, double *part2, int g2, double *out2, cudaStream_t s);
+cudaError_t launch_validate_init(const double *mass, const double *x, const double *v, int64_t n, int32_t *flag,
+                                 cudaStream_t s);
+cudaError_t launch_validate_state(const State &st, int64_t n, double dt_min, double dt_max, int32_t *flag,
+                                  cudaStream_t s);
+cudaError_t launch_validate_idx(const int32_t *idx, int64_t m, int64_t n, int32_t *flag, cudaStream_t s);
+cudaError_t launch_check_correct(const State &st, const int32_t *given, const int32_t *cur, int64_t m, double t_pred,
+                                 int32_t *flag, cudaStream_t s);
+
+}  // namespace hg
