@@ -168,8 +168,34 @@ int64_t hg_size(const hg_ctx *ctx);
 /* Message of the last failed call on ctx (never NULL; "" if none).  Owned by ctx. */
 const char *hg_last_error(const hg_ctx *ctx);
 
-/* Message of the last failed hg_init on this thread (ctx does not exist then). */
+/* Message of the last failed hg_init or hg_evaluate_static on this thread
+ * (calls that have no context to hold it). */
 const char *hg_init_error(void);
+
+/* An evaluation that allocates no memory, for callers that must not call
+ * cudaMalloc: code running inside a host application or framework that owns
+ * all device memory through its own pool or arena, or that has fixed its device
+ * memory budget at start-up, or whose work must not be interrupted by the device
+ * synchronization an allocation can cause.  (The paper has no counterpart; it
+ * is a library convenience.)  Computes acc, jerk and snap of the m listed
+ * particles like hg_evaluate, without a context: the caller passes predicted
+ * data directly.
+ *   n          particles, 1 <= n <= 16384 (larger n: HG_EINVAL);
+ *   mass       [n], pos, vel, acc_pred [n][3]: predicted masses, positions,
+ *              velocities and accelerations, FP64, device memory;
+ *   eps        softening >= 0; precision HG_FP64 or HG_MIXED;
+ *   idx        [m] device int32, strictly increasing, in [0, n) (HG_EINVAL otherwise);
+ *   acc, jerk, snap  [m][3] FP64 device outputs; stream  cudaStream_t or NULL.
+ * Its scratch is one fixed array of about 6 MB in the library's device memory,
+ * present on every GPU that loads the library until the process exits.  The
+ * first call on a device looks up that array's address (make it before any
+ * stream capture on that device).  Every call shares the array, so calls whose
+ * work overlaps on the GPU (different streams or threads) race; the call
+ * synchronizes its stream before returning.  Errors as hg_evaluate, message in
+ * hg_init_error(). */
+int hg_evaluate_static(int64_t n, const double *mass, const double *pos, const double *vel, const double *acc_pred,
+                       double eps, int32_t precision, const int32_t *idx, int64_t m, double *acc, double *jerk,
+                       double *snap, void *stream);
 
 /* Release the context and its device memory.  NULL is allowed. */
 void hg_free(hg_ctx *ctx);

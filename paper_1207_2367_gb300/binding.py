@@ -89,6 +89,8 @@ def load(path: str | None = None):
         L.hg_init_error.restype = C.c_char_p
         L.hg_free.argtypes = [P]
         L.hg_free.restype = None
+        L.hg_evaluate_static.argtypes = [I64, P, P, P, P, D, C.c_int32, I32P, I64, P, P, P, P]
+        L.hg_evaluate_static.restype = C.c_int
         for name in ("hg_init", "hg_next_block", "hg_predict", "hg_evaluate", "hg_correct", "hg_step",
                      "hg_advance", "hg_energy", "hg_get_state", "hg_set_state", "hg_get_stats", "hg_get_profile"):
             getattr(L, name).restype = C.c_int
@@ -208,6 +210,16 @@ def hg_get_profile(ctx, reset=False):
     p = hg_profile()
     _check(ctx, load().hg_get_profile(ctx, C.byref(p), int(bool(reset))))
     return {"ms": dict(zip(SECTIONS, list(p.ms))), "block_steps": p.block_steps}
+
+
+def hg_evaluate_static(mass, pos, vel, acc_pred, eps, precision, idx, m, acc, jerk, snap, stream=None):
+    """Context-free evaluation that allocates nothing (device arrays only, n <= 16384)."""
+    s = getattr(stream, "cuda_stream", stream)
+    rc = load().hg_evaluate_static(int(mass.shape[0]), _ptr(mass), _ptr(pos), _ptr(vel), _ptr(acc_pred),
+                                   float(eps), int(precision), _ptr(idx, np.int32), int(m), _ptr(acc),
+                                   _ptr(jerk), _ptr(snap), s)
+    if rc != HG_OK:
+        raise HGError(rc, load().hg_init_error().decode())
 
 
 def hg_size(ctx):

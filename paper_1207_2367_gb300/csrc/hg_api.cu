@@ -387,6 +387,8 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
 
 }  // namespace
 
+void hg::set_call_error(const char *msg) { g_init_err = msg; }
+
 extern "C" {
 
 void hg_default_opts(hg_opts *o)

@@ -125,6 +125,9 @@ struct EvalArgs {
     int32_t *err;
 };
 
+// Message of the last failed context-free call on this thread (hg_api.cu).
+void set_call_error(const char *msg);
+
 // Host-side launchers (hg_eval.cu).
 cudaError_t eval_setup(int device);
 int eval_grid(bool mixed, int num_sms);
