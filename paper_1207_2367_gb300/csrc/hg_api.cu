@@ -32,6 +32,7 @@ struct hg_ctx {
     double *h_stage = nullptr;                     // pinned staging for small uploads
     double *partial = nullptr;
     int64_t pcap = 0;
+    PlanParams pp{};      // evaluation planner inputs
     double *ra = nullptr, *rj = nullptr, *rs = nullptr;
     double *xe = nullptr, *ve = nullptr, *phi_part = nullptr, *e_part = nullptr, *e_out = nullptr;
     int e_splits = 0, e_g2 = 0;
@@ -126,28 +127,22 @@ EvalArgs eval_args(hg_ctx *c, const int64_t *m_dev, int64_t m_host)
     a.idx = c->d_idx;
     a.m_dev = m_dev;
     a.m_host = m_host;
+    a.plan_dev = m_dev ? reinterpret_cast<const Plan *>(c->d_sc->plan) : nullptr;
+    a.plan_host = m_dev ? Plan{} : make_plan(m_host, c->pp);
     a.partial = c->partial;
-    a.pcap = c->pcap;
     a.eps2 = c->eps * c->eps;
     a.guard = c->eps == 0.0 ? 1 : 0;
-    a.tpi_force = c->opts.tpi;
-    a.b_force = c->opts.jsplit;
-    a.plan_grid = c->egrid;
     a.err = &c->d_sc->err;
     return a;
 }
-
-int tile_j(const hg_ctx *c) { return c->mixed ? kTJMixed : kTJF64; }
-int i_per_thread(const hg_ctx *c) { return c->mixed ? kIMixed : kIF64; }
 
 // Evaluation of the list in d_idx (host-known size m) into ra/rj/rs.
 int run_eval_host_m(hg_ctx *c, int64_t m)
 {
     EvalArgs a = eval_args(c, nullptr, m);
-    const Plan p = make_plan(m, c->npad / tile_j(c), i_per_thread(c), c->egrid, a.tpi_force, a.b_force, a.pcap);
-    const int grid = (int)(p.n_items < c->egrid ? p.n_items : c->egrid);
+    const int grid = (int)(a.plan_host.n_items < c->egrid ? a.plan_host.n_items : c->egrid);
     HG_CUDA(c, launch_eval(c->mixed, a, grid, c->stream));
-    HG_CUDA(c, launch_reduce(c->mixed, a, c->egrid, c->ra, c->rj, c->rs, c->stream));
+    HG_CUDA(c, launch_reduce(a, c->ra, c->rj, c->rs, c->stream));
     c->kernels += 2;
     return HG_OK;
 }
@@ -196,14 +191,14 @@ cudaError_t record_external(cudaEvent_t e, cudaStream_t s)
 int enqueue_block_step(hg_ctx *c, cudaStream_t s, const cudaEvent_t *ev)
 {
     if (ev) HG_CUDA(c, record_external(ev[0], s));
-    HG_CUDA(c, launch_next_block(c->st, c->n, c->nb_part, c->nb_cnt, c->d_idx, c->d_sc, 1, s));
+    HG_CUDA(c, launch_next_block(c->st, c->n, c->nb_part, c->nb_cnt, c->d_idx, c->d_sc, 1, c->pp, s));
     if (ev) HG_CUDA(c, record_external(ev[1], s));
     HG_CUDA(c, launch_predict(c->mixed, c->st, c->rec, c->n, c->npad, &c->d_sc->t_cur, 0.0, &c->d_sc->m, s));
     if (ev) HG_CUDA(c, record_external(ev[2], s));
     EvalArgs a = eval_args(c, &c->d_sc->m, 0);
     HG_CUDA(c, launch_eval(c->mixed, a, c->egrid, s));
     if (ev) HG_CUDA(c, record_external(ev[3], s));
-    HG_CUDA(c, launch_reduce(c->mixed, a, c->egrid, c->ra, c->rj, c->rs, s));
+    HG_CUDA(c, launch_reduce(a, c->ra, c->rj, c->rs, s));
     if (ev) HG_CUDA(c, record_external(ev[4], s));
     HG_CUDA(c, launch_correct(c->st, c->d_idx, &c->d_sc->m, 0, c->n, c->ra, c->rj, c->rs, step_params(c), s));
     if (ev) HG_CUDA(c, record_external(ev[5], s));
@@ -325,7 +320,7 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
     c->nb_cnt = dalloc<int32_t>(c, g);
     c->d_sc = dalloc<DevScalars>(c, 1);
     // Partial sums: b * m <= pcap (b never exceeds the number of j-tiles).
-    const int64_t max_tiles = c->npad / (tile_j(c));
+    const int64_t max_tiles = c->npad / (c->mixed ? kTJMixed : kTJF64);
     int64_t pcap = 4 * n > (1 << 20) ? 4 * n : (1 << 20);
     if (pcap > max_tiles * n) pcap = max_tiles * n;
     c->pcap = pcap;
@@ -346,6 +341,7 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
 
     HG_CUDA(c, eval_setup(c->device));
     c->egrid = eval_grid(c->mixed, c->num_sms);
+    c->pp = plan_params(c->mixed, c->npad, c->num_sms, c->pcap, c->opts.tpi, c->opts.jsplit);
 
     DevScalars z{};
     z.t_stop = INFINITY;
@@ -465,7 +461,7 @@ int hg_init(hg_ctx **out, int64_t n, const double *mass, const double *pos, cons
 int hg_next_block(hg_ctx *c, double *t_next, int32_t *idx, int64_t cap, int64_t *m_out)
 {
     if (!c) return HG_EINVAL;
-    HG_CUDA(c, launch_next_block(c->st, c->n, c->nb_part, c->nb_cnt, c->d_idx, c->d_sc, 0, c->stream));
+    HG_CUDA(c, launch_next_block(c->st, c->n, c->nb_part, c->nb_cnt, c->d_idx, c->d_sc, 0, c->pp, c->stream));
     c->kernels += 3;
     int rc = sync_scalars(c);
     if (rc) return rc;

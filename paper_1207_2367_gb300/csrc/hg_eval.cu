@@ -32,6 +32,9 @@ struct Mixed {
     struct IData {
         float xh, yh, zh, xl, yl, zl, vx, vy, vz, ax, ay, az;
     };
+    struct ITile {
+        IData d[I];
+    };
     struct Acc {
         float hi[I][9], lo[I][9];
     };
@@ -57,6 +60,12 @@ struct Mixed {
             for (int c = 0; c < 9; ++c) a.hi[k][c] = a.lo[k][c] = 0.f;
     }
 
+    __device__ static void load(const Records &rec, const int (&ids)[I], ITile &t)
+    {
+#pragma unroll
+        for (int k = 0; k < I; ++k) load_i(rec, ids[k], t.d[k]);
+    }
+
     __device__ static void issue(const Records &rec, int64_t tile, unsigned char *dst, uint64_t *bar)
     {
         const int64_t j0 = tile * TJ;
@@ -69,7 +78,9 @@ struct Mixed {
 
     // One pair: r_ij = r_j - r_i from (hi, lo) parts, v_ij, a_ij, softened r^2,
     // alpha r^2 = r.v, beta r^2 = v^2 + r.a + alpha^2 r^2, and
-    // A = m r / r^3, J = m v / r^3 - 3 alpha A, S = m a / r^3 - 6 alpha J - 3 beta A.
+    // A = m r / r^3, J = m v / r^3 - 3 alpha A, S = m a / r^3 - 6 alpha J - 3 beta A,
+    // written as A = q r, J = q w, S = q u with q = m / r^3, w = v - 3 alpha r and
+    // u = a - 6 alpha w - 3 beta r, so that each sum takes one FMA per component.
     template <bool GUARD>
     __device__ __forceinline__ static void pair(const IData &d, const float4 p0, const float4 p1,
                                                 const float4 p2, const float az, const float eps2,
@@ -86,27 +97,24 @@ struct Mixed {
         rinv = fmaf(0.5f * rinv, fmaf(-r2 * rinv, rinv, 1.f), rinv);
         if (GUARD) rinv = (r2 > 0.f) ? rinv : 0.f;
         const float rinv2 = rinv * rinv;
-        const float mr3 = p0.w * rinv * rinv2;
+        const float q = p0.w * rinv * rinv2;
         const float rv = fmaf(dz, dvz, fmaf(dy, dvy, dx * dvx));
         const float v2ra =
             fmaf(dz, daz, fmaf(dy, day, fmaf(dx, dax, fmaf(dvz, dvz, fmaf(dvy, dvy, dvx * dvx)))));
         const float alpha = rv * rinv2;
         const float beta = fmaf(alpha, alpha, v2ra * rinv2);
-        const float Ax = mr3 * dx, Ay = mr3 * dy, Az = mr3 * dz;
         const float a3 = -3.f * alpha;
-        const float Jx = fmaf(a3, Ax, mr3 * dvx);
-        const float Jy = fmaf(a3, Ay, mr3 * dvy);
-        const float Jz = fmaf(a3, Az, mr3 * dvz);
-        const float a6 = -6.f * alpha, b3 = -3.f * beta;
-        s[0] += Ax;
-        s[1] += Ay;
-        s[2] += Az;
-        s[3] += Jx;
-        s[4] += Jy;
-        s[5] += Jz;
-        s[6] += fmaf(b3, Ax, fmaf(a6, Jx, mr3 * dax));
-        s[7] += fmaf(b3, Ay, fmaf(a6, Jy, mr3 * day));
-        s[8] += fmaf(b3, Az, fmaf(a6, Jz, mr3 * daz));
+        const float a6 = a3 + a3, b3 = -3.f * beta;
+        const float wx = fmaf(a3, dx, dvx), wy = fmaf(a3, dy, dvy), wz = fmaf(a3, dz, dvz);
+        s[0] = fmaf(q, dx, s[0]);
+        s[1] = fmaf(q, dy, s[1]);
+        s[2] = fmaf(q, dz, s[2]);
+        s[3] = fmaf(q, wx, s[3]);
+        s[4] = fmaf(q, wy, s[4]);
+        s[5] = fmaf(q, wz, s[5]);
+        s[6] = fmaf(q, fmaf(b3, dx, fmaf(a6, wx, dax)), s[6]);
+        s[7] = fmaf(q, fmaf(b3, dy, fmaf(a6, wy, day)), s[7]);
+        s[8] = fmaf(q, fmaf(b3, dz, fmaf(a6, wz, daz)), s[8]);
     }
 
     // Kahan step: hi + x with the running compensation lo (true sum = hi - lo).
@@ -119,7 +127,7 @@ struct Mixed {
     }
 
     template <bool GUARD>
-    __device__ static void tile(const unsigned char *sb, int tpi, int lane_j, const IData (&iv)[I], Acc &acc,
+    __device__ static void tile(const unsigned char *sb, int tpi, int lane_j, const ITile &iv, Acc &acc,
                                 Eps eps2)
     {
         const float4 *r0 = reinterpret_cast<const float4 *>(sb);
@@ -140,7 +148,7 @@ struct Mixed {
                 const float4 p0 = r0[jj], p1 = r1[jj], p2 = r2[jj];
                 const float az = r3[jj];
 #pragma unroll
-                for (int k = 0; k < I; ++k) pair<GUARD>(iv[k], p0, p1, p2, az, eps2, ch[k]);
+                for (int k = 0; k < I; ++k) pair<GUARD>(iv.d[k], p0, p1, p2, az, eps2, ch[k]);
             }
 #pragma unroll
             for (int k = 0; k < I; ++k)
@@ -169,6 +177,9 @@ struct F64 {
     struct IData {
         double x, y, z, vx, vy, vz, ax, ay, az;
     };
+    struct ITile {
+        IData d[I];
+    };
     struct Acc {
         double s[I][9];
     };
@@ -194,6 +205,12 @@ struct F64 {
             for (int c = 0; c < 9; ++c) a.s[k][c] = 0.0;
     }
 
+    __device__ static void load(const Records &rec, const int (&ids)[I], ITile &t)
+    {
+#pragma unroll
+        for (int k = 0; k < I; ++k) load_i(rec, ids[k], t.d[k]);
+    }
+
     __device__ static void issue(const Records &rec, int64_t tile, unsigned char *dst, uint64_t *bar)
     {
         const int64_t j0 = tile * TJ;
@@ -215,30 +232,27 @@ struct F64 {
         double rinv = rsqrt(r2);
         if (GUARD) rinv = (r2 > 0.0) ? rinv : 0.0;
         const double rinv2 = rinv * rinv;
-        const double mr3 = q1.y * rinv * rinv2;
+        const double q = q1.y * rinv * rinv2;
         const double rv = fma(dz, dvz, fma(dy, dvy, dx * dvx));
         const double v2ra = fma(dz, daz, fma(dy, day, fma(dx, dax, fma(dvz, dvz, fma(dvy, dvy, dvx * dvx)))));
         const double alpha = rv * rinv2;
         const double beta = fma(alpha, alpha, v2ra * rinv2);
-        const double Ax = mr3 * dx, Ay = mr3 * dy, Az = mr3 * dz;
         const double a3 = -3.0 * alpha;
-        const double Jx = fma(a3, Ax, mr3 * dvx);
-        const double Jy = fma(a3, Ay, mr3 * dvy);
-        const double Jz = fma(a3, Az, mr3 * dvz);
-        const double a6 = -6.0 * alpha, b3 = -3.0 * beta;
-        s[0] += Ax;
-        s[1] += Ay;
-        s[2] += Az;
-        s[3] += Jx;
-        s[4] += Jy;
-        s[5] += Jz;
-        s[6] += fma(b3, Ax, fma(a6, Jx, mr3 * dax));
-        s[7] += fma(b3, Ay, fma(a6, Jy, mr3 * day));
-        s[8] += fma(b3, Az, fma(a6, Jz, mr3 * daz));
+        const double a6 = a3 + a3, b3 = -3.0 * beta;
+        const double wx = fma(a3, dx, dvx), wy = fma(a3, dy, dvy), wz = fma(a3, dz, dvz);
+        s[0] = fma(q, dx, s[0]);
+        s[1] = fma(q, dy, s[1]);
+        s[2] = fma(q, dz, s[2]);
+        s[3] = fma(q, wx, s[3]);
+        s[4] = fma(q, wy, s[4]);
+        s[5] = fma(q, wz, s[5]);
+        s[6] = fma(q, fma(b3, dx, fma(a6, wx, dax)), s[6]);
+        s[7] = fma(q, fma(b3, dy, fma(a6, wy, day)), s[7]);
+        s[8] = fma(q, fma(b3, dz, fma(a6, wz, daz)), s[8]);
     }
 
     template <bool GUARD>
-    __device__ static void tile(const unsigned char *sb, int tpi, int lane_j, const IData (&iv)[I], Acc &acc,
+    __device__ static void tile(const unsigned char *sb, int tpi, int lane_j, const ITile &iv, Acc &acc,
                                 Eps eps2)
     {
         const double2 *q0 = reinterpret_cast<const double2 *>(sb);
@@ -249,7 +263,7 @@ struct F64 {
             const double2 a = q0[jj], b = q0[TJ + jj], c = q0[2 * TJ + jj], d = q0[3 * TJ + jj],
                           e = q0[4 * TJ + jj];
 #pragma unroll
-            for (int k = 0; k < I; ++k) pair<GUARD>(iv[k], a, b, c, d, e, eps2, acc.s[k]);
+            for (int k = 0; k < I; ++k) pair<GUARD>(iv.d[k], a, b, c, d, e, eps2, acc.s[k]);
         }
     }
 
@@ -261,6 +275,8 @@ struct F64 {
             for (int c = 0; c < 9; ++c) out[k][c] = a.s[k][c];
     }
 };
+
+typedef Mixed MixedEval;
 
 template <class P>
 constexpr size_t smem_bytes()
@@ -280,7 +296,7 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
     const int64_t m = args.m_dev ? *args.m_dev : args.m_host;
     if (m <= 0) return;
     const int64_t ntiles = args.npad / P::TJ;
-    const Plan pl = make_plan(m, ntiles, P::I, args.plan_grid, args.tpi_force, args.b_force, args.pcap);
+    const Plan pl = args.plan_dev ? *args.plan_dev : args.plan_host;
     if ((int64_t)blockIdx.x >= pl.n_items) return;
 
     if (tid == 0) {
@@ -302,14 +318,16 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
         const int64_t tb = split * pl.tiles_per_split;
         const int nt = (int)((ntiles - tb) < pl.tiles_per_split ? (ntiles - tb) : pl.tiles_per_split);
 
-        typename P::IData iv[P::I];
+        typename P::ITile iv;
         int64_t qi[P::I];
+        int ids[P::I];
 #pragma unroll
         for (int k = 0; k < P::I; ++k) {
             qi[k] = itile * pl.ti + (int64_t)slot * P::I + k;
             const int64_t qc = qi[k] < m ? qi[k] : m - 1;
-            P::load_i(args.rec, args.idx[qc], iv[k]);
+            ids[k] = args.idx[qc];
         }
+        P::load(args.rec, ids, iv);
         typename P::Acc acc;
         P::zero(acc);
 
@@ -388,11 +406,11 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
 
 // Table 1 section 4: sum the b j-chunk partials of every listed particle in
 // chunk order and scatter them to acc/jerk/snap [m][3].
-__global__ void k_reduce(const EvalArgs args, int tj, int ipt, double *ra, double *rj, double *rs)
+__global__ void k_reduce(const EvalArgs args, double *ra, double *rj, double *rs)
 {
     const int64_t m = args.m_dev ? *args.m_dev : args.m_host;
     if (m <= 0) return;
-    const Plan pl = make_plan(m, args.npad / tj, ipt, args.plan_grid, args.tpi_force, args.b_force, args.pcap);
+    const Plan pl = args.plan_dev ? *args.plan_dev : args.plan_host;
     const int64_t total = m * 9;
     if (pl.b <= 32) {
         // Few chunks: one thread per (particle, component), chunks in order.
@@ -446,24 +464,24 @@ int occupancy()
 cudaError_t eval_setup(int)
 {
     cudaError_t e;
-    if ((e = set_attr<Mixed, false>()) != cudaSuccess) return e;
-    if ((e = set_attr<Mixed, true>()) != cudaSuccess) return e;
+    if ((e = set_attr<MixedEval, false>()) != cudaSuccess) return e;
+    if ((e = set_attr<MixedEval, true>()) != cudaSuccess) return e;
     if ((e = set_attr<F64, false>()) != cudaSuccess) return e;
     return set_attr<F64, true>();
 }
 
 int eval_grid(bool mixed, int num_sms)
 {
-    return (mixed ? occupancy<Mixed, false>() : occupancy<F64, false>()) * num_sms;
+    return (mixed ? occupancy<MixedEval, false>() : occupancy<F64, false>()) * num_sms;
 }
 
 cudaError_t launch_eval(bool mixed, const EvalArgs &args, int grid, cudaStream_t st)
 {
     if (mixed) {
         if (args.guard)
-            k_eval<Mixed, true><<<grid, kEvalThreads, smem_bytes<Mixed>(), st>>>(args);
+            k_eval<MixedEval, true><<<grid, kEvalThreads, smem_bytes<MixedEval>(), st>>>(args);
         else
-            k_eval<Mixed, false><<<grid, kEvalThreads, smem_bytes<Mixed>(), st>>>(args);
+            k_eval<MixedEval, false><<<grid, kEvalThreads, smem_bytes<MixedEval>(), st>>>(args);
     } else {
         if (args.guard)
             k_eval<F64, true><<<grid, kEvalThreads, smem_bytes<F64>(), st>>>(args);
@@ -473,11 +491,29 @@ cudaError_t launch_eval(bool mixed, const EvalArgs &args, int grid, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce(bool mixed, const EvalArgs &args, int, double *ra, double *rj, double *rs,
-                          cudaStream_t st)
+cudaError_t launch_reduce(const EvalArgs &args, double *ra, double *rj, double *rs, cudaStream_t st)
 {
-    k_reduce<<<1024, 256, 0, st>>>(args, mixed ? Mixed::TJ : F64::TJ, mixed ? Mixed::I : F64::I, ra, rj, rs);
+    k_reduce<<<1024, 256, 0, st>>>(args, ra, rj, rs);
     return cudaGetLastError();
+}
+
+// Overheads in units of one thread's j-iteration (I interactions): per tile the
+// barrier and the bulk-copy issue; per work item the pipeline fill, the lane
+// reduction and the partial-sum stores.  The FP64 iteration is ~30x longer than
+// the mixed one, so its per-item overhead is relatively small.
+PlanParams plan_params(bool mixed, int64_t npad, int num_sms, int64_t pcap, int tpi_force, int b_force)
+{
+    PlanParams q;
+    q.tj = mixed ? MixedEval::TJ : F64::TJ;
+    q.i_per_thread = mixed ? MixedEval::I : F64::I;
+    q.ntiles = npad / q.tj;
+    q.pcap = pcap;
+    q.grid = eval_grid(mixed, num_sms);
+    q.tpi_force = tpi_force;
+    q.b_force = b_force;
+    q.c_tile = mixed ? 2 : 1;
+    q.c_item = mixed ? 24 : 2;
+    return q;
 }
 
 }  // namespace hg

@@ -22,6 +22,7 @@ struct DevScalars {
     int32_t err;           // error bits (ERR_*)
     int32_t flag;          // scratch result of validation kernels
     int32_t pad;
+    int64_t plan[6];       // evaluation plan of the current block (a Plan, written on the device)
 };
 
 enum : int32_t { ERR_TIMEOUT = 1, ERR_BADIDX = 2, ERR_STATE = 4, ERR_VALUE = 8 };
@@ -63,51 +64,71 @@ constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 // of its arguments: the evaluation and the reduction compute the same plan.
 // ---------------------------------------------------------------------------
 struct Plan {
-    int tpi, ti, b;
+    int tpi, ti, b, pad;
     int64_t n_itiles, tiles_per_split, n_items;
 };
 
-__host__ __device__ inline Plan make_plan(int64_t m, int64_t ntiles, int i_per_thread, int grid,
-                                          int tpi_force, int b_force, int64_t pcap)
+// Inputs of the planner that do not change between block steps.
+struct PlanParams {
+    int64_t ntiles;      // j-tiles of npad records
+    int64_t pcap;        // b * m <= pcap (partial-sum capacity)
+    int i_per_thread, tj, grid;
+    int tpi_force, b_force;
+    int c_tile, c_item;  // per-tile and per-item overhead, in j-iterations of one thread
+};
+
+// Candidate c in [0, kPlanCandidates): threads per i = 2^(c / 32), tiles per
+// split from kTps[c % 32].
+constexpr int kPlanCandidates = 7 * 32;
+__host__ __device__ inline int64_t plan_tps(int k)
 {
-    Plan p;
-    int tpi = 1;
-    if (tpi_force > 0) {
-        tpi = tpi_force;
-    } else {
-        int64_t want = (int64_t)kEvalThreads * i_per_thread / (m > 0 ? m : 1);
-        while (tpi * 2 <= want && tpi < kMaxTPI) tpi *= 2;
+    const int64_t t[32] = {1,  2,  3,  4,  5,  6,   7,   8,   9,   10,  11,   12,   13,   14,   15,   16,
+                           20, 24, 32, 40, 48, 64, 96, 128, 192, 256, 384, 512, 1024, 2048, 4096, 8192};
+    return t[k];
+}
+
+// Fill p for candidate c and return its modelled cost (-1: not admissible).
+// cost = waves * (tiles per item * (TJ / tpi + c_tile) + c_item), integers only
+// so that host and device choose the same plan.
+__host__ __device__ inline int64_t plan_candidate(int64_t m, const PlanParams &q, int c, Plan &p)
+{
+    const int tpi = 1 << (c / 32);
+    if (tpi > kMaxTPI || (q.tpi_force > 0 && tpi != q.tpi_force)) return -1;
+    int64_t tps = plan_tps(c % 32);
+    if (q.b_force > 0) {
+        if (c % 32 != 0) return -1;
+        const int64_t b = q.b_force < q.ntiles ? q.b_force : q.ntiles;
+        tps = (q.ntiles + b - 1) / b;
     }
+    if (tps > q.ntiles) return -1;
+    const int64_t b = (q.ntiles + tps - 1) / tps;
+    const int64_t mm = m > 0 ? m : 1;
+    if (b * mm > q.pcap && b > 1) return -1;
     p.tpi = tpi;
-    p.ti = kEvalThreads / tpi * i_per_thread;
-    p.n_itiles = (m + p.ti - 1) / p.ti;
-    int64_t b;
-    if (b_force > 0) {
-        b = b_force;
-    } else {
-        // Aim at >= 2 items per resident CTA; for large blocks pick the split
-        // (1..4) with the least wave quantization loss.
-        int64_t target = 2 * (int64_t)grid;
-        b = (target + p.n_itiles - 1) / p.n_itiles;
-        if (b <= 1) {
-            double best = -1.0;
-            b = 1;
-            for (int64_t c = 1; c <= 4; ++c) {
-                double items = (double)(p.n_itiles * c);
-                double waves = items / grid;
-                double eff = waves / (double)((int64_t)(waves + 0.999999999));
-                if (eff > best + 1e-3) { best = eff; b = c; }
-            }
+    p.ti = kEvalThreads / tpi * q.i_per_thread;
+    p.n_itiles = (mm + p.ti - 1) / p.ti;
+    p.tiles_per_split = tps;
+    p.b = (int)b;
+    p.pad = 0;
+    p.n_items = p.n_itiles * b;
+    const int64_t waves = (p.n_items + q.grid - 1) / q.grid;
+    return waves * (tps * (q.tj / tpi + q.c_tile) + q.c_item);
+}
+
+// The cheapest admissible candidate (ties: lowest candidate index).
+__host__ __device__ inline Plan make_plan(int64_t m, const PlanParams &q)
+{
+    Plan best{}, p{};
+    int64_t best_cost = -1;
+    for (int c = 0; c < kPlanCandidates; ++c) {
+        const int64_t cost = plan_candidate(m, q, c, p);
+        if (cost >= 0 && (best_cost < 0 || cost < best_cost)) {
+            best_cost = cost;
+            best = p;
         }
     }
-    int64_t mcap = m > 0 ? m : 1;
-    if (b * mcap > pcap) b = pcap / mcap;
-    if (b < 1) b = 1;
-    if (b > ntiles) b = ntiles;
-    p.tiles_per_split = (ntiles + b - 1) / b;
-    p.b = (int)((ntiles + p.tiles_per_split - 1) / p.tiles_per_split);   // no empty chunk
-    p.n_items = p.n_itiles * p.b;
-    return p;
+    if (best_cost < 0) plan_candidate(m, q, 0, best);   // unreachable: candidate 0 is admissible
+    return best;
 }
 
 struct EvalArgs {
@@ -116,14 +137,17 @@ struct EvalArgs {
     const int32_t *idx;      // active list (device)
     const int64_t *m_dev;    // block size on the device (graph mode), or nullptr
     int64_t m_host;          // block size when m_dev == nullptr
+    const Plan *plan_dev;    // plan on the device (graph mode), or nullptr
+    Plan plan_host;          // plan when plan_dev == nullptr
     double *partial;         // [b][m][9] partial sums
-    int64_t pcap;            // capacity of partial in units of 9 doubles
     double eps2;
     int guard;               // eps == 0: skip r^2 == 0 pairs
-    int tpi_force, b_force;
-    int plan_grid;           // grid size the plan is made for (launch grid may be smaller)
     int32_t *err;
 };
+
+// Planner inputs of one precision (hg_eval.cu): tiles, tile size, i per thread,
+// overhead constants and the persistent grid of the evaluation kernel.
+PlanParams plan_params(bool mixed, int64_t npad, int num_sms, int64_t pcap, int tpi_force, int b_force);
 
 // Message of the last failed context-free call on this thread (hg_api.cu).
 void set_call_error(const char *msg);
@@ -133,8 +157,7 @@ cudaError_t eval_setup(int device);
 int eval_grid(bool mixed, int num_sms);
 cudaError_t launch_eval(bool mixed, const EvalArgs &args, int grid, cudaStream_t st);
 // Sums the b partials of each listed particle into res_{a,j,s} [m][3].
-cudaError_t launch_reduce(bool mixed, const EvalArgs &args, int eval_grid, double *ra, double *rj,
-                          double *rs, cudaStream_t st);
+cudaError_t launch_reduce(const EvalArgs &args, double *ra, double *rj, double *rs, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // PTX helpers: mbarrier and bulk (TMA) copies global -> shared.

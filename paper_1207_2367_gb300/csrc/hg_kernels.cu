@@ -80,10 +80,41 @@ __global__ void __launch_bounds__(kNBThreads) k_nb_count(const double *t, const 
     if (threadIdx.x == 0) cnt[blockIdx.x] = (int32_t)c;
 }
 
+// The evaluation plan for block size m, by one warp: lane l scores candidates
+// l, l + 32, ...; the lowest cost wins, ties to the lowest candidate index
+// (the same choice make_plan makes on the host).
+__device__ void plan_on_device(int64_t m, const PlanParams &q, DevScalars *sc)
+{
+    const int lane = threadIdx.x & 31;
+    int64_t best = -1;
+    int bc = 0x7fffffff;
+    Plan p;
+    for (int c = lane; c < kPlanCandidates; c += 32) {
+        const int64_t cost = plan_candidate(m, q, c, p);
+        if (cost >= 0 && (best < 0 || cost < best)) {
+            best = cost;
+            bc = c;
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const int64_t ob = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oc = __shfl_xor_sync(0xffffffffu, bc, off);
+        if (ob >= 0 && (best < 0 || ob < best || (ob == best && oc < bc))) {
+            best = ob;
+            bc = oc;
+        }
+    }
+    if (lane == 0) {
+        plan_candidate(m, q, best >= 0 ? bc : 0, p);
+        Plan *dst = reinterpret_cast<Plan *>(sc->plan);
+        *dst = p;
+    }
+}
+
 __global__ void __launch_bounds__(kNBThreads) k_nb_scatter(const double *t, const double *dt, int64_t n,
                                                            int64_t chunk, const double *part, int g,
                                                            const int32_t *cnt, int32_t *idx, DevScalars *sc,
-                                                           int count_step)
+                                                           int count_step, const PlanParams pq)
 {
     __shared__ double sh[32];
     __shared__ int64_t shi[32];
@@ -113,6 +144,7 @@ __global__ void __launch_bounds__(kNBThreads) k_nb_scatter(const double *t, cons
                 sc->interactions += tot * n;
             }
         }
+        if (threadIdx.x < 32) plan_on_device(tot, pq, sc);
     }
     const int64_t lo = blockIdx.x * chunk, hi = (lo + chunk < n) ? lo + chunk : n;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -310,6 +342,8 @@ __global__ void k_correct(State st, const int32_t *idx, const int64_t *m_dev, in
         const double h = st.dt[i];
         const double t1 = st.t[i] + h;
         const double hh = h / 2.0, h2 = h * h / 10.0, h3 = h * h * h / 120.0;
+        // h is a power of two: its reciprocal powers are exact.
+        const double ih = 1.0 / h, ih3 = ih * ih * ih, ih4 = ih3 * ih, ih5 = ih4 * ih;
         double d[6][3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -325,9 +359,9 @@ __global__ void k_correct(State st, const int32_t *idx, const int64_t *m_dev, in
             d[0][k] = a1;
             d[1][k] = j1;
             d[2][k] = s1;
-            d[3][k] = (60.0 * A - 36.0 * J + 9.0 * S) / (h * h * h);
-            d[4][k] = (360.0 * A - 192.0 * J + 36.0 * S) / (h * h * h * h);
-            d[5][k] = (720.0 * A - 360.0 * J + 60.0 * S) / (h * h * h * h * h);
+            d[3][k] = (60.0 * A - 36.0 * J + 9.0 * S) * ih3;
+            d[4][k] = (360.0 * A - 192.0 * J + 36.0 * S) * ih4;
+            d[5][k] = (720.0 * A - 360.0 * J + 60.0 * S) * ih5;
             st.x[3 * i + k] = x1;
             st.v[3 * i + k] = v1;
             st.a[3 * i + k] = a1;
@@ -532,12 +566,12 @@ inline int grid_for(int64_t work, int threads, int cap)
 int nb_grid(int64_t n) { return (int)((n + kNBChunk - 1) / kNBChunk); }
 
 cudaError_t launch_next_block(const State &st, int64_t n, double *part, int32_t *cnt, int32_t *idx, DevScalars *sc,
-                              int count_step, cudaStream_t s)
+                              int count_step, const PlanParams &pq, cudaStream_t s)
 {
     const int g = nb_grid(n);
     k_nb_min<<<g, kNBThreads, 0, s>>>(st.t, st.dt, n, kNBChunk, part);
     k_nb_count<<<g, kNBThreads, 0, s>>>(st.t, st.dt, n, kNBChunk, part, g, cnt);
-    k_nb_scatter<<<g, kNBThreads, 0, s>>>(st.t, st.dt, n, kNBChunk, part, g, cnt, idx, sc, count_step);
+    k_nb_scatter<<<g, kNBThreads, 0, s>>>(st.t, st.dt, n, kNBChunk, part, g, cnt, idx, sc, count_step, pq);
     return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 struct Slot {
     bool ready = false;
     unsigned char *base = nullptr;   // device address of g_scratch on this device
-    int egrid_mixed = 0, egrid_f64 = 0;
+    int sms = 0;
 };
 std::mutex g_mu;
 Slot g_slots[kMaxDevices];
@@ -129,8 +129,7 @@ int setup(int dev, Slot **out)
             return HG_ECUDA;
         }
         s.base = static_cast<unsigned char *>(p);
-        s.egrid_mixed = eval_grid(true, sms);
-        s.egrid_f64 = eval_grid(false, sms);
+        s.sms = sms;
         s.ready = true;
     }
     *out = &s;
@@ -227,19 +226,16 @@ extern "C" int hg_evaluate_static(int64_t n, const double *mass, const double *p
     a.idx = idx;
     a.m_dev = nullptr;
     a.m_host = m;
+    a.plan_dev = nullptr;
+    const PlanParams pq = plan_params(mixed, npad, slot->sms, kStaticPcap, 0, 0);
+    a.plan_host = make_plan(m, pq);
     a.partial = reinterpret_cast<double *>(base + kRecBytes);
-    a.pcap = kStaticPcap;
     a.eps2 = eps * eps;
     a.guard = eps == 0.0 ? 1 : 0;
-    a.tpi_force = 0;
-    a.b_force = 0;
-    a.plan_grid = mixed ? slot->egrid_mixed : slot->egrid_f64;
     a.err = err;
-    const Plan p = make_plan(m, npad / (mixed ? kTJMixed : kTJF64), mixed ? kIMixed : kIF64, a.plan_grid, 0, 0,
-                             a.pcap);
-    const int grid = (int)(p.n_items < a.plan_grid ? p.n_items : a.plan_grid);
+    const int grid = (int)(a.plan_host.n_items < pq.grid ? a.plan_host.n_items : pq.grid);
     if (cudaGetLastError() != cudaSuccess || launch_eval(mixed, a, grid, st) != cudaSuccess ||
-        launch_reduce(mixed, a, a.plan_grid, acc, jerk, snap, st) != cudaSuccess) {
+        launch_reduce(a, acc, jerk, snap, st) != cudaSuccess) {
         set_call_error("launch failed");
         return HG_ECUDA;
     }
