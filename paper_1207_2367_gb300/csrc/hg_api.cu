@@ -26,7 +26,7 @@ struct hg_ctx {
     bool own_stream = false;
     State st{}, st2{};
     Records rec{};
-    int32_t *d_idx = nullptr, *d_idx2 = nullptr, *nb_cnt = nullptr;
+    int32_t *d_idx = nullptr, *d_idx2 = nullptr, *nb_cnt = nullptr, *nb_off = nullptr;
     double *nb_part = nullptr;
     DevScalars *d_sc = nullptr, *h_sc = nullptr;   // h_sc: pinned host mirror
     double *h_stage = nullptr;                     // pinned staging for small uploads
@@ -100,13 +100,14 @@ bool alloc_state(hg_ctx *c, State &s)
     s.mass = dalloc<double>(c, n);
     s.t = dalloc<double>(c, n);
     s.dt = dalloc<double>(c, n);
+    s.tend = dalloc<double>(c, n);
     s.x = dalloc<double>(c, 3 * n);
     s.v = dalloc<double>(c, 3 * n);
     s.a = dalloc<double>(c, 3 * n);
     s.j = dalloc<double>(c, 3 * n);
     s.s = dalloc<double>(c, 3 * n);
     s.c = dalloc<double>(c, 3 * n);
-    return s.mass && s.t && s.dt && s.x && s.v && s.a && s.j && s.s && s.c;
+    return s.mass && s.t && s.dt && s.tend && s.x && s.v && s.a && s.j && s.s && s.c;
 }
 
 StepParams step_params(const hg_ctx *c)
@@ -191,7 +192,7 @@ cudaError_t record_external(cudaEvent_t e, cudaStream_t s)
 int enqueue_block_step(hg_ctx *c, cudaStream_t s, const cudaEvent_t *ev)
 {
     if (ev) HG_CUDA(c, record_external(ev[0], s));
-    HG_CUDA(c, launch_next_block(c->st, c->n, c->nb_part, c->nb_cnt, c->d_idx, c->d_sc, 1, c->pp, s));
+    HG_CUDA(c, launch_next_block(c->st, c->n, c->nb_part, c->nb_cnt, c->nb_off, c->d_idx, c->d_sc, 1, c->pp, s));
     if (ev) HG_CUDA(c, record_external(ev[1], s));
     HG_CUDA(c, launch_predict(c->mixed, c->st, c->rec, c->n, c->npad, &c->d_sc->t_cur, 0.0, &c->d_sc->m, s));
     if (ev) HG_CUDA(c, record_external(ev[2], s));
@@ -318,6 +319,7 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
     const int g = nb_grid(n);
     c->nb_part = dalloc<double>(c, g);
     c->nb_cnt = dalloc<int32_t>(c, g);
+    c->nb_off = dalloc<int32_t>(c, g);
     c->d_sc = dalloc<DevScalars>(c, 1);
     // Partial sums: b * m <= pcap (b never exceeds the number of j-tiles).
     const int64_t max_tiles = c->npad / (c->mixed ? kTJMixed : kTJF64);
@@ -335,7 +337,7 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
     c->e_g2 = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
     c->e_part = dalloc<double>(c, 2 * c->e_g2);
     c->e_out = dalloc<double>(c, 2);
-    ok = ok && c->d_idx && c->d_idx2 && c->nb_part && c->nb_cnt && c->d_sc && c->partial && c->ra && c->rj &&
+    ok = ok && c->d_idx && c->d_idx2 && c->nb_part && c->nb_cnt && c->nb_off && c->d_sc && c->partial && c->ra && c->rj &&
          c->rs && c->xe && c->ve && c->phi_part && c->e_part && c->e_out;
     if (!ok) return fail(c, HG_ENOMEM, "device allocation failed");
 
@@ -363,6 +365,7 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
     if (c->opts.start_mode == 1) {
         std::vector<double> dtv((size_t)n, c->opts.dt_max);
         HG_CUDA(c, cudaMemcpyAsync(c->st.dt, dtv.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        HG_CUDA(c, launch_tend(c->st, n, c->stream));
         rc = sync_scalars(c);
         if (rc) return rc;
         invalidate(c);
@@ -461,7 +464,8 @@ int hg_init(hg_ctx **out, int64_t n, const double *mass, const double *pos, cons
 int hg_next_block(hg_ctx *c, double *t_next, int32_t *idx, int64_t cap, int64_t *m_out)
 {
     if (!c) return HG_EINVAL;
-    HG_CUDA(c, launch_next_block(c->st, c->n, c->nb_part, c->nb_cnt, c->d_idx, c->d_sc, 0, c->pp, c->stream));
+    HG_CUDA(c, launch_next_block(c->st, c->n, c->nb_part, c->nb_cnt, c->nb_off, c->d_idx, c->d_sc, 0, c->pp,
+                                 c->stream));
     c->kernels += 3;
     int rc = sync_scalars(c);
     if (rc) return rc;
@@ -678,6 +682,7 @@ int hg_set_state(hg_ctx *c, const hg_state *in)
              {d.s, s.s, 3 * n},   {d.c, s.c, 3 * n}, {d.t, s.t, n},     {d.dt, s.dt, n}};
     for (auto &q : g)
         HG_CUDA(c, cudaMemcpyAsync(q.dst, q.src, q.len * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    HG_CUDA(c, launch_tend(c->st, n, c->stream));
     rc = upload_scalar(c, &c->d_sc->t_cur, in->t_sys);
     if (rc) return rc;
     invalidate(c);

@@ -23,13 +23,16 @@ struct DevScalars {
     int32_t flag;          // scratch result of validation kernels
     int32_t pad;
     int64_t plan[6];       // evaluation plan of the current block (a Plan, written on the device)
+    int64_t tnext_bits;    // bit pattern of min_i tend_i (next-block pass 1)
+    uint32_t arrive[2];    // CTAs done in next-block passes 1 and 2 (the last one resets it)
 };
 
 enum : int32_t { ERR_TIMEOUT = 1, ERR_BADIDX = 2, ERR_STATE = 4, ERR_VALUE = 8 };
 
 // FP64 state of every particle at its own time, structure of arrays.
+// tend = t + dt (exact: dyadic) is kept beside t and dt for the block selection.
 struct State {
-    double *mass, *x, *v, *a, *j, *s, *c, *t, *dt;
+    double *mass, *x, *v, *a, *j, *s, *c, *t, *dt, *tend;
 };
 
 // ---------------------------------------------------------------------------

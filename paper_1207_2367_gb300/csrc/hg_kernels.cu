@@ -10,23 +10,7 @@
 namespace hg {
 namespace {
 
-constexpr int kNBThreads = 1024;
-
-__device__ __forceinline__ double block_min(double v, double *sh)
-{
-    for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off));
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        v = (l < (int)(blockDim.x >> 5)) ? sh[l] : INFINITY;
-        for (int off = 16; off > 0; off >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, off));
-        if (l == 0) sh[0] = v;
-    }
-    __syncthreads();
-    return sh[0];
-}
+constexpr int kNBThreads = 256;
 
 __device__ __forceinline__ int64_t block_sum_i64(int64_t v, int64_t *sh)
 {
@@ -46,38 +30,27 @@ __device__ __forceinline__ int64_t block_sum_i64(int64_t v, int64_t *sh)
 
 // ------------------------------------------------------------------------
 // Table 1 section 1: next block time and the ascending list of due particles.
-// Three passes over t_i + dt_i (exact: all times are dyadic), one CTA per
-// contiguous chunk, no atomics: results do not depend on scheduling.
+// Times are dyadic and non-negative, so tend_i = t_i + dt_i is exact and its
+// IEEE bit pattern orders like its value: the passes compare 64-bit integers.
+// One CTA per contiguous chunk; the last CTA to finish a pass (atomic arrival
+// count, no waiting) completes it: pass 1 the global minimum, pass 2 the
+// chunk offsets, m and the evaluation plan.  Results do not depend on the
+// order in which CTAs run.
 // ------------------------------------------------------------------------
-__global__ void __launch_bounds__(kNBThreads) k_nb_min(const double *t, const double *dt, int64_t n, int64_t chunk,
-                                                       double *part)
+__device__ __forceinline__ long long block_min_ll(long long v, long long *sh)
 {
-    __shared__ double sh[32];
-    const int64_t lo = blockIdx.x * chunk, hi = (lo + chunk < n) ? lo + chunk : n;
-    double v = INFINITY;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) v = fmin(v, t[i] + dt[i]);
-    v = block_min(v, sh);
-    if (threadIdx.x == 0) part[blockIdx.x] = v;
-}
-
-__device__ __forceinline__ double global_min(const double *part, int g, double *sh)
-{
-    double v = INFINITY;
-    for (int c = threadIdx.x; c < g; c += blockDim.x) v = fmin(v, part[c]);
-    return block_min(v, sh);
-}
-
-__global__ void __launch_bounds__(kNBThreads) k_nb_count(const double *t, const double *dt, int64_t n, int64_t chunk,
-                                                         const double *part, int g, int32_t *cnt)
-{
-    __shared__ double sh[32];
-    __shared__ int64_t shi[32];
-    const double tn = global_min(part, g, sh);
-    const int64_t lo = blockIdx.x * chunk, hi = (lo + chunk < n) ? lo + chunk : n;
-    int64_t c = 0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) c += (t[i] + dt[i] == tn) ? 1 : 0;
-    c = block_sum_i64(c, shi);
-    if (threadIdx.x == 0) cnt[blockIdx.x] = (int32_t)c;
+    for (int off = 16; off > 0; off >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, off));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = (l < (int)(blockDim.x >> 5)) ? sh[l] : LLONG_MAX;
+        for (int off = 16; off > 0; off >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, off));
+        if (l == 0) sh[0] = v;
+    }
+    __syncthreads();
+    return sh[0];
 }
 
 // The evaluation plan for block size m, by one warp: lane l scores candidates
@@ -111,55 +84,132 @@ __device__ void plan_on_device(int64_t m, const PlanParams &q, DevScalars *sc)
     }
 }
 
-__global__ void __launch_bounds__(kNBThreads) k_nb_scatter(const double *t, const double *dt, int64_t n,
-                                                           int64_t chunk, const double *part, int g,
-                                                           const int32_t *cnt, int32_t *idx, DevScalars *sc,
-                                                           int count_step, const PlanParams pq)
+
+// True in every thread of the CTA that arrives last (counter reset for reuse).
+__device__ __forceinline__ bool last_to_arrive(uint32_t *counter, uint32_t total, int *sh_flag)
 {
-    __shared__ double sh[32];
-    __shared__ int64_t shi[32];
-    __shared__ int32_t woff[33];
-    const double tn = global_min(part, g, sh);
-    const double t_stop = sc->t_stop;
-    if (tn > t_stop) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            sc->m = 0;
-            sc->done = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t prev = atomicAdd(counter, 1u);
+        *sh_flag = (prev == total - 1) ? 1 : 0;
+        if (*sh_flag) {
+            *counter = 0u;
+            __threadfence();
         }
-        return;
     }
-    int64_t pre = 0;
-    for (int c = threadIdx.x; c < (int)blockIdx.x; c += blockDim.x) pre += cnt[c];
-    pre = block_sum_i64(pre, shi);
-    if (blockIdx.x == 0) {
-        int64_t tot = 0;
-        for (int c = threadIdx.x; c < g; c += blockDim.x) tot += cnt[c];
-        tot = block_sum_i64(tot, shi);
-        if (threadIdx.x == 0) {
+    __syncthreads();
+    return *sh_flag != 0;
+}
+
+__global__ void __launch_bounds__(kNBThreads) k_nb_min(const double *tend, int64_t n, int64_t chunk,
+                                                       long long *part, int g, DevScalars *sc)
+{
+    __shared__ long long sh[32];
+    __shared__ int last;
+    const long long *bits = reinterpret_cast<const long long *>(tend);
+    const int64_t lo = blockIdx.x * chunk, hi = (lo + chunk < n) ? lo + chunk : n;
+    long long v = LLONG_MAX;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) v = min(v, __ldg(bits + i));
+    v = block_min_ll(v, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
+    if (!last_to_arrive(&sc->arrive[0], (uint32_t)g, &last)) return;
+    __threadfence();
+    v = LLONG_MAX;
+    for (int c = threadIdx.x; c < g; c += blockDim.x) v = min(v, *((volatile long long *)part + c));
+    v = block_min_ll(v, sh);
+    if (threadIdx.x == 0) sc->tnext_bits = v;
+}
+
+__global__ void __launch_bounds__(kNBThreads) k_nb_count(const double *tend, int64_t n, int64_t chunk,
+                                                         int32_t *cnt, int32_t *off, int g, DevScalars *sc,
+                                                         int count_step, const PlanParams pq)
+{
+    __shared__ long long shl[32];
+    __shared__ int64_t shi[32];
+    __shared__ int last;
+    const long long tn = *((volatile long long *)&sc->tnext_bits);
+    const long long *bits = reinterpret_cast<const long long *>(tend);
+    const int64_t lo = blockIdx.x * chunk, hi = (lo + chunk < n) ? lo + chunk : n;
+    int64_t c = 0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) c += (__ldg(bits + i) == tn) ? 1 : 0;
+    c = block_sum_i64(c, shi);
+    if (threadIdx.x == 0) cnt[blockIdx.x] = (int32_t)c;
+    if (!last_to_arrive(&sc->arrive[1], (uint32_t)g, &last)) return;
+    __threadfence();
+    // Exclusive prefix of the chunk counts: each thread scans a run of chunks.
+    const int per = (g + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int c0 = threadIdx.x * per, c1 = (c0 + per < g) ? c0 + per : g;
+    int64_t run = 0;
+    for (int k = c0; k < c1; ++k) run += *((volatile int32_t *)cnt + k);
+    // block exclusive scan of the runs
+    int64_t incl = run;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (l >= o) incl += u;
+    }
+    __syncthreads();
+    if (l == 31) shi[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int64_t x = (l < (int)(blockDim.x >> 5)) ? shi[l] : 0;
+        int64_t xi = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t u = __shfl_up_sync(0xffffffffu, xi, o);
+            if (l >= o) xi += u;
+        }
+        shi[l] = xi - x;   // exclusive warp offsets
+        if (l == 31) shl[0] = xi;   // total
+    }
+    __syncthreads();
+    int64_t base = shi[w] + incl - run;
+    for (int k = c0; k < c1; ++k) {
+        off[k] = (int32_t)base;
+        base += *((volatile int32_t *)cnt + k);
+    }
+    const int64_t tot = shl[0];
+    const double t_next = __longlong_as_double(tn);
+    const bool take = t_next <= sc->t_stop;
+    if (threadIdx.x == 0) {
+        if (take) {
             sc->m = tot;
-            sc->t_cur = tn;
+            sc->t_cur = t_next;
             sc->done = 0;
             if (count_step) {
                 sc->steps += 1;
                 sc->interactions += tot * n;
             }
+        } else {
+            sc->m = 0;
+            sc->done = 1;
         }
-        if (threadIdx.x < 32) plan_on_device(tot, pq, sc);
     }
+    if (take && threadIdx.x < 32) plan_on_device(tot, pq, sc);
+}
+
+__global__ void __launch_bounds__(kNBThreads) k_nb_scatter(const double *tend, int64_t n, int64_t chunk,
+                                                           const int32_t *off, int32_t *idx, const DevScalars *sc)
+{
+    __shared__ int32_t woff[33];
+    if (*((volatile int64_t *)&sc->m) <= 0) return;
+    const long long tn = *((volatile long long *)&sc->tnext_bits);
+    const long long *bits = reinterpret_cast<const long long *>(tend);
+    int64_t pre = off[blockIdx.x];
     const int64_t lo = blockIdx.x * chunk, hi = (lo + chunk < n) ? lo + chunk : n;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     for (int64_t base = lo; base < hi; base += blockDim.x) {
         const int64_t i = base + threadIdx.x;
-        const bool due = (i < hi) && (t[i] + dt[i] == tn);
+        const bool due = (i < hi) && (__ldg(bits + i) == tn);
         const unsigned ball = __ballot_sync(0xffffffffu, due);
         if (l == 0) woff[w] = __popc(ball);
         __syncthreads();
         if (w == 0) {
-            int v = (l < (int)(blockDim.x >> 5)) ? woff[l] : 0;
+            const int v = (l < (int)(blockDim.x >> 5)) ? woff[l] : 0;
             int incl = v;
-            for (int off = 1; off < 32; off <<= 1) {
-                const int u = __shfl_up_sync(0xffffffffu, incl, off);
-                if (l >= off) incl += u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (l >= o) incl += u;
             }
             woff[l] = incl - v;
             if (l == 31) woff[32] = incl;
@@ -326,6 +376,7 @@ __global__ void k_start(State st, int64_t n, const double *ra, const double *rj,
         }
         st.t[i] = 0.0;
         st.dt[i] = block_dt_init(criterion(sp.eta_init, 4, d), sp.dt_min, sp.dt_max);
+        st.tend[i] = st.dt[i];
     }
 }
 
@@ -333,6 +384,45 @@ __global__ void k_start(State st, int64_t n, const double *ra, const double *rj,
 // Sect. 3 item 3: corrector, Hermite interpolation for crackle/pop/a^(5),
 // p = 6 criterion and the new block step, for the m particles of the block.
 // ------------------------------------------------------------------------
+
+// Component k of particle i over its step h: corrected v and r (stored, with
+// the new a, jerk, snap and crackle), and crackle, pop and a^(5) from the
+// degree-5 interpolant through a, jerk, snap at both ends of the step.
+__device__ __forceinline__ void correct_component(const State &st, int64_t i, int k, double h, double a1, double j1,
+                                                  double s1, double &c3, double &c4, double &c5)
+{
+    const double hh = h / 2.0, h2 = h * h / 10.0, h3 = h * h * h / 120.0;
+    // h is a power of two: its reciprocal powers are exact.
+    const double ih = 1.0 / h, ih3 = ih * ih * ih, ih4 = ih3 * ih, ih5 = ih4 * ih;
+    const int64_t q = 3 * i + k;
+    const double x0 = st.x[q], v0 = st.v[q], a0 = st.a[q], j0 = st.j[q], s0 = st.s[q];
+    const double v1 = v0 + hh * (a1 + a0) - h2 * (j1 - j0) + h3 * (s1 + s0);
+    const double x1 = x0 + hh * (v1 + v0) - h2 * (a1 - a0) + h3 * (j1 + j0);
+    const double A = a1 - a0 - j0 * h - s0 * h * h / 2.0;
+    const double J = (j1 - j0 - s0 * h) * h;
+    const double S = (s1 - s0) * h * h;
+    c3 = (60.0 * A - 36.0 * J + 9.0 * S) * ih3;
+    c4 = (360.0 * A - 192.0 * J + 36.0 * S) * ih4;
+    c5 = (720.0 * A - 360.0 * J + 60.0 * S) * ih5;
+    st.x[q] = x1;
+    st.v[q] = v1;
+    st.a[q] = a1;
+    st.j[q] = j1;
+    st.s[q] = s1;
+    st.c[q] = c3;
+}
+
+// New time and p = 6 step of particle i from d = a^(0..5) at the step's end.
+__device__ __forceinline__ void finish_step(const State &st, int64_t i, double h, const double (*d)[3],
+                                            const StepParams &sp)
+{
+    const double t1 = st.t[i] + h;
+    const double dt1 = block_dt(criterion(sp.eta, 6, d), h, t1, sp.dt_min, sp.dt_max);
+    st.t[i] = t1;
+    st.dt[i] = dt1;
+    st.tend[i] = t1 + dt1;
+}
+
 __global__ void k_correct(State st, const int32_t *idx, const int64_t *m_dev, int64_t m_host, const double *ra,
                           const double *rj, const double *rs, StepParams sp)
 {
@@ -340,39 +430,22 @@ __global__ void k_correct(State st, const int32_t *idx, const int64_t *m_dev, in
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = idx[q];
         const double h = st.dt[i];
-        const double t1 = st.t[i] + h;
-        const double hh = h / 2.0, h2 = h * h / 10.0, h3 = h * h * h / 120.0;
-        // h is a power of two: its reciprocal powers are exact.
-        const double ih = 1.0 / h, ih3 = ih * ih * ih, ih4 = ih3 * ih, ih5 = ih4 * ih;
         double d[6][3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const double x0 = st.x[3 * i + k], v0 = st.v[3 * i + k], a0 = st.a[3 * i + k];
-            const double j0 = st.j[3 * i + k], s0 = st.s[3 * i + k];
-            const double a1 = ra[3 * q + k], j1 = rj[3 * q + k], s1 = rs[3 * q + k];
-            const double v1 = v0 + hh * (a1 + a0) - h2 * (j1 - j0) + h3 * (s1 + s0);
-            const double x1 = x0 + hh * (v1 + v0) - h2 * (a1 - a0) + h3 * (j1 + j0);
-            // Degree-5 interpolant through a, jerk, snap at both ends.
-            const double A = a1 - a0 - j0 * h - s0 * h * h / 2.0;
-            const double J = (j1 - j0 - s0 * h) * h;
-            const double S = (s1 - s0) * h * h;
-            d[0][k] = a1;
-            d[1][k] = j1;
-            d[2][k] = s1;
-            d[3][k] = (60.0 * A - 36.0 * J + 9.0 * S) * ih3;
-            d[4][k] = (360.0 * A - 192.0 * J + 36.0 * S) * ih4;
-            d[5][k] = (720.0 * A - 360.0 * J + 60.0 * S) * ih5;
-            st.x[3 * i + k] = x1;
-            st.v[3 * i + k] = v1;
-            st.a[3 * i + k] = a1;
-            st.j[3 * i + k] = j1;
-            st.s[3 * i + k] = s1;
-            st.c[3 * i + k] = d[3][k];
+            double c3, c4, c5;
+            correct_component(st, i, k, h, ra[3 * q + k], rj[3 * q + k], rs[3 * q + k], c3, c4, c5);
+            d[0][k] = ra[3 * q + k];
+            d[1][k] = rj[3 * q + k];
+            d[2][k] = rs[3 * q + k];
+            d[3][k] = c3;
+            d[4][k] = c4;
+            d[5][k] = c5;
         }
-        st.t[i] = t1;
-        st.dt[i] = block_dt(criterion(sp.eta, 6, d), h, t1, sp.dt_min, sp.dt_max);
+        finish_step(st, i, h, d, sp);
     }
 }
+
 
 // ------------------------------------------------------------------------
 // Energy: Sect. 2 softened potential, W = -1/2 sum_i m_i sum_{j != i} m_j /
@@ -516,7 +589,7 @@ __global__ void k_validate_init(const double *mass, const double *x, const doubl
 __global__ void k_validate_state(const State st, int64_t n, double dt_min, double dt_max, int32_t *flag)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        bool ok = isfinite(st.mass[i]) && st.mass[i] > 0.0 && isfinite(st.t[i]);
+        bool ok = isfinite(st.mass[i]) && st.mass[i] > 0.0 && isfinite(st.t[i]) && st.t[i] >= 0.0;
         for (int k = 0; k < 3; ++k) {
             const int64_t q = 3 * i + k;
             ok = ok && isfinite(st.x[q]) && isfinite(st.v[q]) && isfinite(st.a[q]) && isfinite(st.j[q]) &&
@@ -551,6 +624,13 @@ __global__ void k_check_correct(const State st, const int32_t *given, const int3
     }
 }
 
+// tend = t + dt for every particle (after the state is replaced).
+__global__ void k_tend(State st, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        st.tend[i] = st.t[i] + st.dt[i];
+}
+
 inline int grid_for(int64_t work, int threads, int cap)
 {
     int64_t g = (work + threads - 1) / threads;
@@ -565,24 +645,31 @@ inline int grid_for(int64_t work, int threads, int cap)
 // ---------------------------------------------------------------------------
 int nb_grid(int64_t n) { return (int)((n + kNBChunk - 1) / kNBChunk); }
 
-cudaError_t launch_next_block(const State &st, int64_t n, double *part, int32_t *cnt, int32_t *idx, DevScalars *sc,
-                              int count_step, const PlanParams &pq, cudaStream_t s)
+cudaError_t launch_next_block(const State &st, int64_t n, double *part, int32_t *cnt, int32_t *off, int32_t *idx,
+                              DevScalars *sc, int count_step, const PlanParams &pq, cudaStream_t s)
 {
     const int g = nb_grid(n);
-    k_nb_min<<<g, kNBThreads, 0, s>>>(st.t, st.dt, n, kNBChunk, part);
-    k_nb_count<<<g, kNBThreads, 0, s>>>(st.t, st.dt, n, kNBChunk, part, g, cnt);
-    k_nb_scatter<<<g, kNBThreads, 0, s>>>(st.t, st.dt, n, kNBChunk, part, g, cnt, idx, sc, count_step, pq);
+    long long *bits = reinterpret_cast<long long *>(part);
+    k_nb_min<<<g, kNBThreads, 0, s>>>(st.tend, n, kNBChunk, bits, g, sc);
+    k_nb_count<<<g, kNBThreads, 0, s>>>(st.tend, n, kNBChunk, cnt, off, g, sc, count_step, pq);
+    k_nb_scatter<<<g, kNBThreads, 0, s>>>(st.tend, n, kNBChunk, off, idx, sc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tend(const State &st, int64_t n, cudaStream_t s)
+{
+    k_tend<<<grid_for(n, 256, 4096), 256, 0, s>>>(st, n);
     return cudaGetLastError();
 }
 
 cudaError_t launch_predict(bool mixed, const State &st, const Records &rec, int64_t n, int64_t npad,
                            const double *t_dev, double t_host, const int64_t *m_dev, cudaStream_t s)
 {
-    const int g = grid_for(npad, 256, 1 << 20);
+    const int g = grid_for(npad, 64, 1 << 20);   // small CTAs: even spread of the FP64 work
     if (mixed)
-        k_predict<true><<<g, 256, 0, s>>>(st, rec, n, npad, t_dev, t_host, m_dev);
+        k_predict<true><<<g, 64, 0, s>>>(st, rec, n, npad, t_dev, t_host, m_dev);
     else
-        k_predict<false><<<g, 256, 0, s>>>(st, rec, n, npad, t_dev, t_host, m_dev);
+        k_predict<false><<<g, 64, 0, s>>>(st, rec, n, npad, t_dev, t_host, m_dev);
     return cudaGetLastError();
 }
 
@@ -596,7 +683,8 @@ cudaError_t launch_start(const State &st, int64_t n, const double *ra, const dou
 cudaError_t launch_correct(const State &st, const int32_t *idx, const int64_t *m_dev, int64_t m_host, int64_t n_max,
                            const double *ra, const double *rj, const double *rs, const StepParams &sp, cudaStream_t s)
 {
-    k_correct<<<grid_for(n_max, 128, 4096), 128, 0, s>>>(st, idx, m_dev, m_host, ra, rj, rs, sp);
+    // One warp per CTA: the FP64 pipe is the limit, so spread small blocks over many SMs.
+    k_correct<<<grid_for(n_max, 32, 16384), 32, 0, s>>>(st, idx, m_dev, m_host, ra, rj, rs, sp);
     return cudaGetLastError();
 }
 

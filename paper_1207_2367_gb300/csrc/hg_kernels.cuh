@@ -9,11 +9,14 @@ struct StepParams {
     double eta, eta_init, dt_min, dt_max;
 };
 
-constexpr int64_t kNBChunk = 4096;   // particles per CTA in the next-block passes
+constexpr int64_t kNBChunk = 2048;   // particles per CTA in the next-block passes
 
 int nb_grid(int64_t n);
-cudaError_t launch_next_block(const State &st, int64_t n, double *part, int32_t *cnt, int32_t *idx, DevScalars *sc,
-                              int count_step, const PlanParams &pq, cudaStream_t s);
+// part, cnt, off: nb_grid(n) entries each.
+cudaError_t launch_next_block(const State &st, int64_t n, double *part, int32_t *cnt, int32_t *off, int32_t *idx,
+                              DevScalars *sc, int count_step, const PlanParams &pq, cudaStream_t s);
+// tend = t + dt after the state was replaced.
+cudaError_t launch_tend(const State &st, int64_t n, cudaStream_t s);
 cudaError_t launch_predict(bool mixed, const State &st, const Records &rec, int64_t n, int64_t npad,
                            const double *t_dev, double t_host, const int64_t *m_dev, cudaStream_t s);
 cudaError_t launch_start(const State &st, int64_t n, const double *ra, const double *rj, const double *rs,
