@@ -151,7 +151,8 @@ int hg_energy(hg_ctx *ctx, double *kinetic, double *potential);
 
 /* Copy the state out (every non-NULL field) / replace it (every field required).
  * hg_set_state checks: masses > 0, finite values, dt a power of two in
- * [dt_min, dt_max], t_i a multiple of dt_i; it invalidates any prediction. */
+ * [dt_min, dt_max], t_i >= 0 and a multiple of dt_i; it invalidates any
+ * prediction. */
 int hg_get_state(hg_ctx *ctx, hg_state *out);
 int hg_set_state(hg_ctx *ctx, const hg_state *in);
 

@@ -247,6 +247,35 @@ __device__ __forceinline__ Pred predict_one(const State &st, int64_t i, double t
     return p;
 }
 
+// FP64 <-> FP32 conversions done with integer operations on the IEEE-754
+// encodings (binary64: 1 sign, 11 exponent bits, bias 1023, 52 fraction bits;
+// binary32: 1, 8, bias 127, 23).  GB300's FP64 pipe, which also executes the
+// hardware conversions, is the predictor's limit; the integer pipes are not.
+// d2f: round to nearest, ties to even; results below the smallest normal float
+// (2^-126) become zero of the same sign.  Inputs are finite.
+__device__ __forceinline__ float d2f(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7ffu) - 1023 + 127;
+    unsigned int m = (unsigned int)((b >> 29) & 0x7fffffu);
+    const unsigned int rem = (unsigned int)b & 0x1fffffffu;
+    m += (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;   // may carry into e
+    const unsigned int mag = ((unsigned int)e << 23) + m;
+    return __uint_as_float(e <= 0 ? sign : (sign | mag));
+}
+
+// Exact widening of a float that is zero or normal.
+__device__ __forceinline__ double f2d(float f)
+{
+    const unsigned int u = __float_as_uint(f);
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    const unsigned int e = (u >> 23) & 0xffu;
+    const unsigned long long mag =
+        ((unsigned long long)(e + (1023u - 127u)) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)(e == 0u ? sign : (sign | mag)));
+}
+
 template <bool MIXED>
 __global__ void k_predict(const State st, const Records rec, int64_t n, int64_t npad, const double *t_dev,
                           double t_host, const int64_t *m_dev)
@@ -258,18 +287,29 @@ __global__ void k_predict(const State st, const Records rec, int64_t n, int64_t 
             float4 r0, r1, r2;
             float r3;
             if (i < n) {
-                const Pred p = predict_one(st, i, tt);
-                float hi[3], lo[3];
+                // Positions: FP64 Taylor series, then split into float hi + lo.
+                // Velocities and accelerations feed only the FP32 pair
+                // arithmetic: FP32 Horner series from the rounded derivatives.
+                const double h = tt - st.t[i];
+                const double h2 = h * h * 0.5, h3 = h2 * h * (1.0 / 3.0), h4 = h3 * h * 0.25, h5 = h4 * h * 0.2;
+                const float hf = d2f(h);
+                float hi[3], lo[3], vp[3], ap[3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    hi[k] = __double2float_rn(p.x[k]);
-                    lo[k] = __double2float_rn(p.x[k] - (double)hi[k]);
+                    const int64_t q = 3 * i + k;
+                    const double x = st.x[q], v = st.v[q], a = st.a[q], j = st.j[q], s = st.s[q], c = st.c[q];
+                    const double xp = x + fma(h, v, fma(h2, a, fma(h3, j, fma(h4, s, h5 * c))));
+                    hi[k] = d2f(xp);
+                    lo[k] = d2f(xp - f2d(hi[k]));
+                    const float vf = d2f(v), af = d2f(a), jf = d2f(j), sf = d2f(s), cf = d2f(c);
+                    vp[k] = fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, cf * (1.f / 24.f), sf * (1.f / 6.f)), jf * 0.5f), af),
+                                 vf);
+                    ap[k] = fmaf(hf, fmaf(hf, fmaf(hf, cf * (1.f / 6.f), sf * 0.5f), jf), af);
                 }
-                r0 = make_float4(hi[0], hi[1], hi[2], __double2float_rn(st.mass[i]));
-                r1 = make_float4(lo[0], lo[1], lo[2], __double2float_rn(p.a[0]));
-                r2 = make_float4(__double2float_rn(p.v[0]), __double2float_rn(p.v[1]), __double2float_rn(p.v[2]),
-                                 __double2float_rn(p.a[1]));
-                r3 = __double2float_rn(p.a[2]);
+                r0 = make_float4(hi[0], hi[1], hi[2], d2f(st.mass[i]));
+                r1 = make_float4(lo[0], lo[1], lo[2], ap[0]);
+                r2 = make_float4(vp[0], vp[1], vp[2], ap[1]);
+                r3 = ap[2];
             } else {
                 const float far = (float)kPadCoord;
                 r0 = make_float4(far, far, far, 0.f);
