@@ -40,6 +40,10 @@ FLOPS_F32 = 77     # FP32 adds + muls of the pair law per interaction (FMA = 2 f
 FLOPS_F64 = 77     # the same count for the FP64 path
 PAPER_FLOPS = 97   # the paper's count per interaction (82 SP + 15 DP)
 NUM_SMS = 152
+# DRAM bytes (read + write) per evaluation-kernel launch on the default workload,
+# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, mean of 100
+# launches, cold L2).  Valid only while that kernel is unchanged.
+EVAL_TRAFFIC = {(65536, "equal", "mixed"): 3.47e6}
 
 
 def parse():
@@ -213,18 +217,31 @@ class Runner:
         return self.hg.hg_energy(self.ctx)
 
 
-def roofline(hg, inter, prof, mixed, mhz, kind):
+def roofline(hg, inter, prof, mixed, mhz, kind, traffic=None):
     eval_s = prof["ms"]["evaluate"] / 1e3
     peak = fp32_peak_tflops(mhz) if mixed else fp64_peak_tflops(mhz)
     flops = FLOPS_F32 if mixed else FLOPS_F64
     ach = inter * flops / eval_s / 1e12 if eval_s > 0 else None
     return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": (ach / peak) if ach else None, "traffic": None,
+            "frac": (ach / peak) if ach else None, "traffic": traffic,
             "kernel": "k_eval<Mixed>" if mixed else "k_eval<F64>",
             "flops_per_interaction": flops,
             "peak_note": ((f"FP32 FMA pipe: {NUM_SMS} SMs x 128 lanes x 2 flops" if mixed else
                            f"FP64 pipe: {NUM_SMS} SMs x 2 DFMA x 2 flops") + f" x {mhz:.0f} MHz ({kind} max clock)"),
             "eval_share_of_step": eval_s / (sum(prof["ms"].values()) / 1e3) if prof["ms"] else None}
+
+
+def aggregate(ms, interactions, dist, device):
+    """Whole-job figures over ranks: the slowest rank's time and the sum of the
+    interactions every rank evaluated (weak scaling)."""
+    if dist is None:
+        return ms, interactions
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([int(interactions)], dtype=torch.int64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(c.item())
 
 
 def run_ours(a, rank, world, dist):
@@ -285,14 +302,7 @@ def run_ours(a, rank, world, dist):
         e = hg.hg_energy(ctx)
     dE_end = abs((sum(e) - E0) / E0)
 
-    ms_max, inter_tot = ms, inter
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-        c = torch.tensor([float(inter)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        inter_tot = int(c.item())
+    ms_max, inter_tot = aggregate(ms, inter, dist, "cuda")
     value = inter_tot / (ms_max / 1e3)
     mhz, kind = sm_max_mhz()
 
@@ -312,7 +322,8 @@ def run_ours(a, rank, world, dist):
                    "l2": "flushed between timed steps (256 MB write outside the timed events); "
                          "inputs resident in HBM",
                    "parallelism": f"replicas x{world}"},
-        "roofline": roofline(hg, inter, prof, mixed, mhz, kind),
+        "roofline": roofline(hg, inter, prof, mixed, mhz, kind,
+                             EVAL_TRAFFIC.get((a.n, a.imf, a.precision)) if a.block_steps == 0 else None),
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,
