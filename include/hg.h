@@ -54,6 +54,10 @@ typedef struct hg_opts {
                                  crackle and t are zero and dt = dt_max until hg_set_state (resume) */
     int32_t profile;          /* 1 = time the sections of every graph-replayed block step with CUDA
                                  events (hg_get_profile); adds a synchronization per graph replay */
+    int32_t test_stall_eval;  /* testing only: 1 = every evaluation expects bytes that are never
+                                 copied, so its bounded waits run out (~2 s) and the call returns
+                                 HG_ETIMEOUT; exercises the failure path without a fault */
+    int32_t reserved;
     double dt_min;            /* smallest step, power of two (default 2^-25, Sect. 3) */
     double dt_max;            /* largest step, power of two (default 2^-3, Sect. 3) */
     double eta_init;          /* accuracy parameter of the first step (p = 4 criterion; default 0.01) */

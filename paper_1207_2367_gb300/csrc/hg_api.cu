@@ -133,6 +133,7 @@ EvalArgs eval_args(hg_ctx *c, const int64_t *m_dev, int64_t m_host)
     a.partial = c->partial;
     a.eps2 = c->eps * c->eps;
     a.guard = c->eps == 0.0 ? 1 : 0;
+    a.tx_extra = c->opts.test_stall_eval ? 16u : 0u;
     a.err = &c->d_sc->err;
     return a;
 }
@@ -402,6 +403,8 @@ void hg_default_opts(hg_opts *o)
     o->graph_steps = 8;
     o->start_mode = 0;
     o->profile = 0;
+    o->test_stall_eval = 0;
+    o->reserved = 0;
     o->dt_min = 1.0 / 33554432.0;   // 2^-25
     o->dt_max = 0.125;              // 2^-3
     o->eta_init = 0.01;
@@ -439,6 +442,7 @@ int hg_init(hg_ctx **out, int64_t n, const double *mass, const double *pos, cons
     if (o.jsplit < 0) return bad("jsplit must be >= 0");
     if (o.graph_steps < 1 || o.graph_steps > 1024) return bad("graph_steps must be in [1, 1024]");
     if (o.start_mode != 0 && o.start_mode != 1) return bad("start_mode must be 0 or 1");
+    if (o.test_stall_eval != 0 && o.test_stall_eval != 1) return bad("test_stall_eval must be 0 or 1");
 
     hg_ctx *c = new (std::nothrow) hg_ctx();
     if (!c) {

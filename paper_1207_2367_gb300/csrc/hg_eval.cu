@@ -66,10 +66,11 @@ struct Mixed {
         for (int k = 0; k < I; ++k) load_i(rec, ids[k], t.d[k]);
     }
 
-    __device__ static void issue(const Records &rec, int64_t tile, unsigned char *dst, uint64_t *bar)
+    __device__ static void issue(const Records &rec, int64_t tile, unsigned char *dst, uint64_t *bar,
+                                 uint32_t tx_extra)
     {
         const int64_t j0 = tile * TJ;
-        mbar_arrive_expect_tx(bar, kStageBytes);
+        mbar_arrive_expect_tx(bar, kStageBytes + tx_extra);
         bulk_g2s(dst, static_cast<const float4 *>(rec.p[0]) + j0, TJ * 16, bar);
         bulk_g2s(dst + TJ * 16, static_cast<const float4 *>(rec.p[1]) + j0, TJ * 16, bar);
         bulk_g2s(dst + TJ * 32, static_cast<const float4 *>(rec.p[2]) + j0, TJ * 16, bar);
@@ -211,10 +212,11 @@ struct F64 {
         for (int k = 0; k < I; ++k) load_i(rec, ids[k], t.d[k]);
     }
 
-    __device__ static void issue(const Records &rec, int64_t tile, unsigned char *dst, uint64_t *bar)
+    __device__ static void issue(const Records &rec, int64_t tile, unsigned char *dst, uint64_t *bar,
+                                 uint32_t tx_extra)
     {
         const int64_t j0 = tile * TJ;
-        mbar_arrive_expect_tx(bar, kStageBytes);
+        mbar_arrive_expect_tx(bar, kStageBytes + tx_extra);
 #pragma unroll
         for (int q = 0; q < 5; ++q)
             bulk_g2s(dst + q * TJ * 16, static_cast<const double2 *>(rec.p[q]) + j0, TJ * 16, bar);
@@ -335,7 +337,7 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
             const int pre = nt < kStages ? nt : kStages;
             for (int s = 0; s < pre; ++s) {
                 const int st = (int)((seq + s) % kStages);
-                P::issue(args.rec, tb + s, smem + st * P::kStageBytes, &bars[st]);
+                P::issue(args.rec, tb + s, smem + st * P::kStageBytes, &bars[st], args.tx_extra);
             }
         }
         for (int t = 0; t < nt; ++t) {
@@ -356,7 +358,7 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
             }
             if (tid == 0 && t + kStages < nt) {
                 fence_proxy_async();
-                P::issue(args.rec, tb + t + kStages, smem + st * P::kStageBytes, &bars[st]);
+                P::issue(args.rec, tb + t + kStages, smem + st * P::kStageBytes, &bars[st], args.tx_extra);
             }
         }
         seq += (uint32_t)nt;

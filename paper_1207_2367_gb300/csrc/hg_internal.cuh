@@ -145,6 +145,7 @@ struct EvalArgs {
     double *partial;         // [b][m][9] partial sums
     double eps2;
     int guard;               // eps == 0: skip r^2 == 0 pairs
+    uint32_t tx_extra;       // testing: bytes expected per tile beyond those copied (0 normally)
     int32_t *err;
 };
 

@@ -1,0 +1,118 @@
+"""GPU runtime behaviour: checkpoint/resume, the bounded-wait failure path, and
+parity at the full sizes of the N = 65536 and N = 2^20 configurations on
+sampled outputs (the oracle evaluates the sampled particles one by one)."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1207_2367_gb300 import inputs
+from gpu_util import DT_MAX, DT_MIN, gpu_state, rel_rows
+
+pytestmark = pytest.mark.gpu
+
+
+def test_resume_from_checkpoint_continues_bitwise(hg):
+    n, eps = 2000, 1e-3
+    p = inputs.plummer(n, 8)
+    o = hg.hg_default_opts(precision=hg.HG_MIXED, dt_max=DT_MAX)
+    a = hg.hg_init(p.mass, p.pos, p.vel, eps, 0.45, o)
+    b = hg.hg_init(p.mass, p.pos, p.vel, eps, 0.45, hg.hg_default_opts(precision=hg.HG_MIXED, dt_max=DT_MAX,
+                                                                         start_mode=1))
+    try:
+        hg.hg_step(a, 30)
+        ck, t_ck = gpu_state(hg, a, n)
+        hg.hg_step(a, 20)
+        hg.hg_set_state(b, ck, t_ck)
+        hg.hg_step(b, 20)
+        sa, ta = gpu_state(hg, a, n)
+        sb, tb = gpu_state(hg, b, n)
+        assert ta == tb
+        for f in hg.STATE_FIELDS:
+            np.testing.assert_array_equal(sa[f], sb[f], err_msg=f)
+    finally:
+        hg.hg_free(a)
+        hg.hg_free(b)
+
+
+def test_bounded_wait_reports_timeout_and_gpu_stays_usable(hg):
+    """A testing option makes every tile wait for bytes that are never copied: the
+    waits run out (~2 s), the call returns HG_ETIMEOUT, and a new context works."""
+    n = 512
+    p = inputs.plummer(n, 3)
+    o = hg.hg_default_opts(precision=hg.HG_MIXED, start_mode=1, test_stall_eval=1)
+    ctx = hg.hg_init(p.mass, p.pos, p.vel, 1e-3, 0.45, o)
+    try:
+        hg.hg_predict(ctx, 0.0)
+        t0 = time.perf_counter()
+        with pytest.raises(hg.HGError) as e:
+            hg.hg_evaluate(ctx, np.arange(8, dtype=np.int32), 8)
+        assert e.value.code == hg.HG_ETIMEOUT
+        assert time.perf_counter() - t0 < 60
+    finally:
+        hg.hg_free(ctx)
+    ctx = hg.hg_init(p.mass, p.pos, p.vel, 1e-3, 0.45, hg.hg_default_opts(precision=hg.HG_MIXED))
+    try:
+        hg.hg_step(ctx, 4)
+        assert hg.hg_get_stats(ctx)["block_steps"] == 4
+    finally:
+        hg.hg_free(ctx)
+
+
+def test_full_size_n65536_fp64_sampled(hg):
+    """Configuration N = 65536 (equal masses, seed 2, eps = 1e-4): start-up
+    evaluation of all particles in FP64, 128 sampled particles vs the oracle."""
+    n, eps = 65536, 1e-4
+    p = inputs.plummer(n, 2)
+    ctx = hg.hg_init(p.mass, p.pos, p.vel, eps, 0.45, hg.hg_default_opts(precision=hg.HG_FP64, dt_max=DT_MAX))
+    try:
+        st, _ = gpu_state(hg, ctx, n)
+    finally:
+        hg.hg_free(ctx)
+    idx = np.sort(np.random.default_rng(2).choice(n, 128, replace=False)).astype(np.int32)
+    ref = oracle.evaluate(p.mass, p.pos, p.vel, np.zeros((n, 3)), eps, idx)
+    for f, r in zip(("acc", "jerk", "snap"), ref):
+        assert rel_rows(st[f][idx], r).max() <= 1e-12, f
+
+
+def test_full_size_n1048576_mixed(hg):
+    """Configuration N = 2^20 (Salpeter masses, seed 3, eps = 1e-4), mixed path:
+    start-up evaluation on 48 sampled particles vs the oracle (normwise and
+    condition-scaled), then after 64 block steps the mixed evaluation of a seeded
+    4096-particle subset against the FP64 GPU path on the same predicted state."""
+    n, eps = 1 << 20, 1e-4
+    p = inputs.plummer(n, 3, imf="salpeter")
+    mixed = hg.hg_init(p.mass, p.pos, p.vel, eps, 0.45, hg.hg_default_opts(precision=hg.HG_MIXED, dt_max=DT_MAX))
+    f64 = None
+    try:
+        st, _ = gpu_state(hg, mixed, n)
+        idx = np.sort(np.random.default_rng(3).choice(n, 48, replace=False)).astype(np.int32)
+        z = np.zeros((n, 3))
+        ref = oracle.evaluate(p.mass, p.pos, p.vel, z, eps, idx)
+        scale = oracle.eval_absum(p.mass, p.pos, p.vel, z, eps, idx)
+        for k, (f, r, tol) in enumerate(zip(("acc", "jerk", "snap"), ref, (1e-6, 1e-5, 1e-4))):
+            g = st[f][idx]
+            assert np.linalg.norm(g - r) / np.linalg.norm(r) <= tol, f
+            assert (np.linalg.norm(g - r, axis=1) / scale[:, k]).max() <= tol, f
+
+        hg.hg_step(mixed, 64)
+        st, t_sys = gpu_state(hg, mixed, n)
+        f64 = hg.hg_init(p.mass, p.pos, p.vel, eps, 0.45,
+                         hg.hg_default_opts(precision=hg.HG_FP64, dt_max=DT_MAX, start_mode=1))
+        hg.hg_set_state(f64, st, t_sys)
+        sub = np.sort(np.random.default_rng(6).choice(n, 4096, replace=False)).astype(np.int32)
+        t = float(np.min(st["t"] + st["dt"]))
+        out = {}
+        for name, c in (("mixed", mixed), ("fp64", f64)):
+            res = [np.empty((4096, 3)) for _ in range(3)]
+            hg.hg_predict(c, t)
+            hg.hg_evaluate(c, sub, 4096, *res)
+            out[name] = res
+        for g, r, tol in zip(out["mixed"], out["fp64"], (1e-6, 1e-5, 1e-4)):
+            assert np.linalg.norm(g - r) / np.linalg.norm(r) <= tol
+            assert np.median(rel_rows(g, r)) <= tol
+    finally:
+        hg.hg_free(mixed)
+        if f64 is not None:
+            hg.hg_free(f64)
