@@ -111,6 +111,18 @@ void hg_default_opts(hg_opts *opts);
 int hg_init(hg_ctx **out, int64_t n, const double *mass, const double *pos, const double *vel,
             double eps, double eta, const hg_opts *opts);
 
+/* Independent clusters in one context: particles [offsets[c], offsets[c+1]) of
+ * the concatenated arrays form cluster c (offsets: n_clusters + 1 int64, host
+ * or device, offsets[0] = 0, offsets[n_clusters] = n, every cluster non-empty).
+ * A particle feels only its own cluster; each cluster keeps its own block-time
+ * hierarchy while all clusters advance together in global block steps (every
+ * particle due at the global next block time is active), evaluated in one
+ * persistent kernel per block step.  Every other call works on the whole set;
+ * hg_energy returns sums over clusters of each cluster's own K and W (FP64
+ * pairs).  n_clusters = 0 is hg_init.  Errors as hg_init. */
+int hg_init_batch(hg_ctx **out, int32_t n_clusters, const int64_t *offsets, int64_t n, const double *mass,
+                  const double *pos, const double *vel, double eps, double eta, const hg_opts *opts);
+
 /* Table 1, section 1: t_next = min_i (t_i + dt_i) and the ascending indices of
  * the m particles with t_i + dt_i == t_next.  Makes them the context's current
  * block.  idx (host or device, capacity cap) receives the list when non-NULL;

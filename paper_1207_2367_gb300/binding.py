@@ -71,6 +71,8 @@ def load(path: str | None = None):
         L.hg_default_opts.argtypes = [C.POINTER(hg_opts)]
         L.hg_default_opts.restype = None
         L.hg_init.argtypes = [C.POINTER(P), I64, P, P, P, D, D, C.POINTER(hg_opts)]
+        L.hg_init_batch.argtypes = [C.POINTER(P), C.c_int32, P, I64, P, P, P, D, D, C.POINTER(hg_opts)]
+        L.hg_init_batch.restype = C.c_int
         L.hg_next_block.argtypes = [P, C.POINTER(D), I32P, I64, C.POINTER(I64)]
         L.hg_predict.argtypes = [P, D]
         L.hg_evaluate.argtypes = [P, I32P, I64, P, P, P]
@@ -141,6 +143,19 @@ def hg_init(mass, pos, vel, eps, eta, opts: hg_opts | None = None):
     ctx = C.c_void_p()
     rc = load().hg_init(C.byref(ctx), n, _ptr(mass), _ptr(pos), _ptr(vel), float(eps), float(eta),
                         C.byref(opts) if opts is not None else None)
+    if rc != HG_OK:
+        raise HGError(rc, load().hg_init_error().decode())
+    return ctx.value
+
+
+def hg_init_batch(offsets, mass, pos, vel, eps, eta, opts: hg_opts | None = None):
+    """Context of independent clusters; offsets: int64 [n_clusters + 1]."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    n = int(mass.shape[0])
+    ctx = C.c_void_p()
+    rc = load().hg_init_batch(C.byref(ctx), int(offsets.shape[0] - 1), offsets.ctypes.data, n, _ptr(mass),
+                              _ptr(pos), _ptr(vel), float(eps), float(eta),
+                              C.byref(opts) if opts is not None else None)
     if rc != HG_OK:
         raise HGError(rc, load().hg_init_error().decode())
     return ctx.value

@@ -33,6 +33,8 @@ struct hg_ctx {
     double *partial = nullptr;
     int64_t pcap = 0;
     PlanParams pp{};      // evaluation planner inputs
+    BatchView bv{};       // independent clusters (bv.nc == 0: one system)
+    std::vector<int64_t> cl_off_host;
     double *ra = nullptr, *rj = nullptr, *rs = nullptr;
     double *xe = nullptr, *ve = nullptr, *phi_part = nullptr, *e_part = nullptr, *e_out = nullptr;
     int e_splits = 0, e_g2 = 0;
@@ -135,14 +137,29 @@ EvalArgs eval_args(hg_ctx *c, const int64_t *m_dev, int64_t m_host)
     a.guard = c->eps == 0.0 ? 1 : 0;
     a.tx_extra = c->opts.test_stall_eval ? 16u : 0u;
     a.err = &c->d_sc->err;
+    a.bv = c->bv;
     return a;
+}
+
+const int32_t *rmap_of(const hg_ctx *c) { return c->bv.nc > 0 ? c->bv.rmap : nullptr; }
+
+// Work list over clusters; in graph steps it also counts the step's pair evaluations.
+cudaError_t batch_plan(hg_ctx *c, const int64_t *m_dev, int64_t m_host, cudaStream_t s)
+{
+    return launch_batch_plan(c->d_idx, m_dev, m_host, c->bv, c->pp.tj, c->pp.i_per_thread, c->egrid, c->pcap,
+                             m_dev ? c->d_sc : nullptr, s);
 }
 
 // Evaluation of the list in d_idx (host-known size m) into ra/rj/rs.
 int run_eval_host_m(hg_ctx *c, int64_t m)
 {
     EvalArgs a = eval_args(c, nullptr, m);
-    const int grid = (int)(a.plan_host.n_items < c->egrid ? a.plan_host.n_items : c->egrid);
+    int grid = (int)(a.plan_host.n_items < c->egrid ? a.plan_host.n_items : c->egrid);
+    if (c->bv.nc > 0) {
+        HG_CUDA(c, batch_plan(c, nullptr, m, c->stream));
+        c->kernels += 1;
+        grid = c->egrid;
+    }
     HG_CUDA(c, launch_eval(c->mixed, a, grid, c->stream));
     HG_CUDA(c, launch_reduce(a, c->ra, c->rj, c->rs, c->stream));
     c->kernels += 2;
@@ -193,9 +210,12 @@ cudaError_t record_external(cudaEvent_t e, cudaStream_t s)
 int enqueue_block_step(hg_ctx *c, cudaStream_t s, const cudaEvent_t *ev)
 {
     if (ev) HG_CUDA(c, record_external(ev[0], s));
-    HG_CUDA(c, launch_next_block(c->st, c->n, c->nb_part, c->nb_cnt, c->nb_off, c->d_idx, c->d_sc, 1, c->pp, s));
+    HG_CUDA(c, launch_next_block(c->st, c->n, c->nb_part, c->nb_cnt, c->nb_off, c->d_idx, c->d_sc,
+                                 c->bv.nc > 0 ? 2 : 1, c->pp, s));
+    if (c->bv.nc > 0) HG_CUDA(c, batch_plan(c, &c->d_sc->m, 0, s));
     if (ev) HG_CUDA(c, record_external(ev[1], s));
-    HG_CUDA(c, launch_predict(c->mixed, c->st, c->rec, c->n, c->npad, &c->d_sc->t_cur, 0.0, &c->d_sc->m, s));
+    HG_CUDA(c, launch_predict(c->mixed, c->st, c->rec, c->n, c->npad, &c->d_sc->t_cur, 0.0, &c->d_sc->m, rmap_of(c),
+                              s));
     if (ev) HG_CUDA(c, record_external(ev[2], s));
     EvalArgs a = eval_args(c, &c->d_sc->m, 0);
     HG_CUDA(c, launch_eval(c->mixed, a, c->egrid, s));
@@ -243,7 +263,7 @@ int replay(hg_ctx *c, bool many)
 {
     HG_CUDA(c, cudaGraphLaunch(many ? c->g_many : c->g_one, c->stream));
     const int steps = many ? c->opts.graph_steps : 1;
-    c->kernels += (int64_t)kStepKernels * steps;
+    c->kernels += (int64_t)(kStepKernels + (c->bv.nc > 0 ? 1 : 0)) * steps;
     if (!c->opts.profile) return HG_OK;
     HG_CUDA(c, cudaStreamSynchronize(c->stream));
     const std::vector<cudaEvent_t> &ev = many ? c->ev_many : c->ev_one;
@@ -301,6 +321,28 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
 
     const int64_t tj = kTJMixed > kTJF64 ? kTJMixed : kTJF64;
     c->npad = (n + tj - 1) / tj * tj;
+    // Clusters: each cluster's records start on a tile boundary of both layouts.
+    const int nc = c->cl_off_host.empty() ? 0 : (int)c->cl_off_host.size() - 1;
+    std::vector<int64_t> rec_off;
+    std::vector<int32_t> rmap, cl_of;
+    int64_t pcap_clusters = 0;
+    if (nc > 0) {
+        rec_off.assign((size_t)nc + 1, 0);
+        rmap.resize((size_t)n);
+        cl_of.resize((size_t)n);
+        for (int k = 0; k < nc; ++k) {
+            const int64_t a = c->cl_off_host[k], b = c->cl_off_host[k + 1];
+            rec_off[k + 1] = rec_off[k] + (b - a + tj - 1) / tj * tj;
+            for (int64_t i = a; i < b; ++i) {
+                rmap[(size_t)i] = (int32_t)(rec_off[k] + (i - a));
+                cl_of[(size_t)i] = k;
+            }
+            const int64_t ntc = (rec_off[k + 1] - rec_off[k]) / (c->mixed ? kTJMixed : kTJF64);
+            pcap_clusters += (ntc + kBatchTpsMax - 1) / kBatchTpsMax * (b - a);
+        }
+        c->npad = rec_off[(size_t)nc];
+        if (c->npad > (int64_t)INT32_MAX) return fail(c, HG_EINVAL, "too many padded records");
+    }
     bool ok = alloc_state(c, c->st) && alloc_state(c, c->st2);
     if (c->mixed) {
         c->rec.p[0] = dalloc<float4>(c, c->npad);
@@ -326,7 +368,30 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
     const int64_t max_tiles = c->npad / (c->mixed ? kTJMixed : kTJF64);
     int64_t pcap = 4 * n > (1 << 20) ? 4 * n : (1 << 20);
     if (pcap > max_tiles * n) pcap = max_tiles * n;
+    if (nc > 0) pcap = 4 * n + pcap_clusters;   // the coarsest batch split always fits
     c->pcap = pcap;
+    if (nc > 0) {
+        BatchView &bv = c->bv;
+        bv.nc = nc;
+        int64_t *clo = dalloc<int64_t>(c, nc + 1), *ro = dalloc<int64_t>(c, nc + 1);
+        int32_t *rm = dalloc<int32_t>(c, n), *co = dalloc<int32_t>(c, n);
+        bv.a_off = dalloc<int64_t>(c, nc + 1);
+        bv.item_off = dalloc<int64_t>(c, nc + 1);
+        bv.part_off = dalloc<int64_t>(c, nc + 1);
+        bv.tpi_c = dalloc<int32_t>(c, nc);
+        bv.b_c = dalloc<int32_t>(c, nc);
+        bv.tps = dalloc<int64_t>(c, 1);
+        if (!clo || !ro || !rm || !co || !bv.a_off || !bv.item_off || !bv.part_off || !bv.tpi_c || !bv.b_c || !bv.tps)
+            return fail(c, HG_ENOMEM, "device allocation failed");
+        HG_CUDA(c, cudaMemcpy(clo, c->cl_off_host.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+        HG_CUDA(c, cudaMemcpy(ro, rec_off.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+        HG_CUDA(c, cudaMemcpy(rm, rmap.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+        HG_CUDA(c, cudaMemcpy(co, cl_of.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+        bv.cl_off = clo;
+        bv.rec_off = ro;
+        bv.rmap = rm;
+        bv.cl_of = co;
+    }
     c->partial = dalloc<double>(c, 9 * pcap);
     c->ra = dalloc<double>(c, 3 * n);
     c->rj = dalloc<double>(c, 3 * n);
@@ -375,7 +440,8 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
     std::vector<int32_t> iota((size_t)n);
     for (int64_t i = 0; i < n; ++i) iota[(size_t)i] = (int32_t)i;
     HG_CUDA(c, cudaMemcpyAsync(c->d_idx, iota.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
-    HG_CUDA(c, launch_predict(c->mixed, c->st, c->rec, n, c->npad, nullptr, 0.0, nullptr, c->stream));
+    if (c->bv.nc > 0) HG_CUDA(c, launch_pad_records(c->mixed, c->rec, c->npad, c->stream));
+    HG_CUDA(c, launch_predict(c->mixed, c->st, c->rec, n, c->npad, nullptr, 0.0, nullptr, rmap_of(c), c->stream));
     rc = run_eval_host_m(c, n);
     if (rc) return rc;
     HG_CUDA(c, launch_start(c->st, n, c->ra, c->rj, c->rs, step_params(c), c->stream));
@@ -416,6 +482,12 @@ const char *hg_init_error(void) { return g_init_err.c_str(); }
 int hg_init(hg_ctx **out, int64_t n, const double *mass, const double *pos, const double *vel, double eps,
             double eta, const hg_opts *opts)
 {
+    return hg_init_batch(out, 0, nullptr, n, mass, pos, vel, eps, eta, opts);
+}
+
+int hg_init_batch(hg_ctx **out, int32_t n_clusters, const int64_t *offsets, int64_t n, const double *mass,
+                  const double *pos, const double *vel, double eps, double eta, const hg_opts *opts)
+{
     g_init_err.clear();
     auto bad = [](const char *m) {
         g_init_err = m;
@@ -424,6 +496,19 @@ int hg_init(hg_ctx **out, int64_t n, const double *mass, const double *pos, cons
     if (!out) return bad("out is NULL");
     *out = nullptr;
     if (n < 1 || n > (int64_t)INT32_MAX - 1024) return bad("n must be in [1, 2^31 - 1025]");
+    std::vector<int64_t> cl;
+    if (n_clusters < 0) return bad("n_clusters must be >= 0");
+    if (n_clusters > 0) {
+        if (!offsets) return bad("offsets are required with clusters");
+        cl.resize((size_t)n_clusters + 1);
+        if (cudaMemcpy(cl.data(), offsets, cl.size() * sizeof(int64_t), cudaMemcpyDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return bad("offsets could not be read");
+        }
+        if (cl[0] != 0 || cl[(size_t)n_clusters] != n) return bad("offsets must start at 0 and end at n");
+        for (int32_t k = 0; k < n_clusters; ++k)
+            if (cl[(size_t)k + 1] <= cl[(size_t)k]) return bad("every cluster needs at least one particle");
+    }
     if (!mass || !pos || !vel) return bad("mass, pos and vel are required");
     if (!isfinite(eps) || eps < 0.0) return bad("eps must be finite and >= 0");
     if (!isfinite(eta) || eta <= 0.0) return bad("eta must be finite and > 0");
@@ -455,6 +540,7 @@ int hg_init(hg_ctx **out, int64_t n, const double *mass, const double *pos, cons
     c->eta = eta;
     c->opts = o;
     c->device = o.device;
+    c->cl_off_host = std::move(cl);
     int rc = init_impl(c, mass, pos, vel);
     if (rc != HG_OK) {
         g_init_err = c->err;
@@ -490,7 +576,7 @@ int hg_predict(hg_ctx *c, double t)
 {
     if (!c) return HG_EINVAL;
     if (!isfinite(t)) return fail(c, HG_EINVAL, "t must be finite");
-    HG_CUDA(c, launch_predict(c->mixed, c->st, c->rec, c->n, c->npad, nullptr, t, nullptr, c->stream));
+    HG_CUDA(c, launch_predict(c->mixed, c->st, c->rec, c->n, c->npad, nullptr, t, nullptr, rmap_of(c), c->stream));
     c->kernels += 1;
     c->t_pred = t;
     c->eval_m = -1;
@@ -622,7 +708,7 @@ int hg_energy(hg_ctx *c, double *kinetic, double *potential)
     const double t = c->h_sc->t_cur;
     c->kernels += 4;
     HG_CUDA(c, launch_energy(c->opts.energy_precision == HG_MIXED, c->st, c->n, t, c->eps * c->eps, c->xe, c->ve,
-                             c->phi_part, c->e_splits, c->e_part, c->e_g2, c->e_out, c->stream));
+                             c->phi_part, c->e_splits, c->e_part, c->e_g2, c->e_out, c->bv, c->stream));
     HG_CUDA(c, cudaMemcpyAsync(c->h_stage, c->e_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     HG_CUDA(c, cudaStreamSynchronize(c->stream));
     if (kinetic) *kinetic = c->h_stage[0];

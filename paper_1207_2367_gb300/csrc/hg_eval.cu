@@ -297,9 +297,12 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
 
     const int64_t m = args.m_dev ? *args.m_dev : args.m_host;
     if (m <= 0) return;
-    const int64_t ntiles = args.npad / P::TJ;
+    const BatchView &bv = args.bv;
+    const bool batch = bv.nc > 0;
     const Plan pl = args.plan_dev ? *args.plan_dev : args.plan_host;
-    if ((int64_t)blockIdx.x >= pl.n_items) return;
+    const int64_t n_items = batch ? bv.item_off[bv.nc] : pl.n_items;
+    const int64_t tps = batch ? *bv.tps : pl.tiles_per_split;
+    if ((int64_t)blockIdx.x >= n_items) return;
 
     if (tid == 0) {
 #pragma unroll
@@ -308,26 +311,57 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
     }
     __syncthreads();
 
-    const int tpi = pl.tpi;
-    const int lane_j = tid & (tpi - 1);
-    const int slot = tid / tpi;
     const typename P::Eps eps2 = (typename P::Eps)args.eps2;
     uint32_t seq = 0;   // tiles consumed so far by this CTA (mbarrier phase bookkeeping)
 
-    for (int64_t item = blockIdx.x; item < pl.n_items; item += gridDim.x) {
-        const int64_t itile = item / pl.b;
-        const int64_t split = item - itile * pl.b;
-        const int64_t tb = split * pl.tiles_per_split;
-        const int nt = (int)((ntiles - tb) < pl.tiles_per_split ? (ntiles - tb) : pl.tiles_per_split);
+    for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+        // Decode the item: active positions [q_begin, q_end) of this i-tile's
+        // system, first i-position of the tile, j-tiles [tbase, tbase + nt),
+        // and the partial-sum row of position q (rbase + q).
+        int tpi;
+        int64_t q_tile, q_end, tbase, rbase, nt64;
+        if (batch) {
+            int lo = 0, hi = bv.nc - 1;            // last cluster with item_off[c] <= item
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (bv.item_off[mid] <= item) lo = mid; else hi = mid - 1;
+            }
+            const int c = lo;
+            tpi = bv.tpi_c[c];
+            const int64_t b = bv.b_c[c];
+            const int64_t local = item - bv.item_off[c];
+            const int64_t itile = local / b, split = local - itile * b;
+            const int64_t qb = bv.a_off[c], mc = bv.a_off[c + 1] - qb;
+            const int64_t ti = kEvalThreads / tpi * P::I;
+            q_tile = qb + itile * ti;
+            q_end = qb + mc;
+            const int64_t t0 = bv.rec_off[c] / P::TJ, ntc = (bv.rec_off[c + 1] - bv.rec_off[c]) / P::TJ;
+            tbase = t0 + split * tps;
+            nt64 = ntc - split * tps < tps ? ntc - split * tps : tps;
+            rbase = bv.part_off[c] + split * mc - qb;
+        } else {
+            tpi = pl.tpi;
+            const int64_t itile = item / pl.b, split = item - itile * pl.b;
+            const int64_t ntiles = args.npad / P::TJ;
+            q_tile = itile * pl.ti;
+            q_end = m;
+            tbase = split * tps;
+            nt64 = ntiles - tbase < tps ? ntiles - tbase : tps;
+            rbase = split * m;
+        }
+        const int nt = (int)nt64;
+        const int lane_j = tid & (tpi - 1);
+        const int slot = tid / tpi;
 
         typename P::ITile iv;
         int64_t qi[P::I];
         int ids[P::I];
 #pragma unroll
         for (int k = 0; k < P::I; ++k) {
-            qi[k] = itile * pl.ti + (int64_t)slot * P::I + k;
-            const int64_t qc = qi[k] < m ? qi[k] : m - 1;
-            ids[k] = args.idx[qc];
+            qi[k] = q_tile + (int64_t)slot * P::I + k;
+            const int64_t qc = qi[k] < q_end ? qi[k] : q_end - 1;
+            const int32_t i = args.idx[qc];
+            ids[k] = batch ? bv.rmap[i] : i;
         }
         P::load(args.rec, ids, iv);
         typename P::Acc acc;
@@ -337,7 +371,7 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
             const int pre = nt < kStages ? nt : kStages;
             for (int s = 0; s < pre; ++s) {
                 const int st = (int)((seq + s) % kStages);
-                P::issue(args.rec, tb + s, smem + st * P::kStageBytes, &bars[st], args.tx_extra);
+                P::issue(args.rec, tbase + s, smem + st * P::kStageBytes, &bars[st], args.tx_extra);
             }
         }
         for (int t = 0; t < nt; ++t) {
@@ -358,7 +392,7 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
             }
             if (tid == 0 && t + kStages < nt) {
                 fence_proxy_async();
-                P::issue(args.rec, tb + t + kStages, smem + st * P::kStageBytes, &bars[st], args.tx_extra);
+                P::issue(args.rec, tbase + t + kStages, smem + st * P::kStageBytes, &bars[st], args.tx_extra);
             }
         }
         seq += (uint32_t)nt;
@@ -396,8 +430,8 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
         if (lane_j == 0) {
 #pragma unroll
             for (int k = 0; k < P::I; ++k) {
-                if (qi[k] < m) {
-                    double *dst = args.partial + ((int64_t)split * m + qi[k]) * 9;
+                if (qi[k] < q_end) {
+                    double *dst = args.partial + (rbase + qi[k]) * 9;
 #pragma unroll
                     for (int c = 0; c < 9; ++c) dst[c] = out[k][c];
                 }
@@ -414,6 +448,24 @@ __global__ void k_reduce(const EvalArgs args, double *ra, double *rj, double *rs
     if (m <= 0) return;
     const Plan pl = args.plan_dev ? *args.plan_dev : args.plan_host;
     const int64_t total = m * 9;
+    if (args.bv.nc > 0) {
+        // Clusters: the chunks of position q are rows part_off[c] + s * m_c + (q - a_off[c]).
+        const BatchView &bv = args.bv;
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+             e += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t q = e / 9;
+            const int c9 = (int)(e - q * 9);
+            const int c = bv.cl_of[args.idx[q]];
+            const int64_t qb = bv.a_off[c], mc = bv.a_off[c + 1] - qb;
+            const int64_t row0 = bv.part_off[c] + (q - qb);
+            const int b = bv.b_c[c];
+            double s = 0.0;
+            for (int sp = 0; sp < b; ++sp) s += args.partial[(row0 + (int64_t)sp * mc) * 9 + c9];
+            double *dst = c9 < 3 ? ra : (c9 < 6 ? rj : rs);
+            dst[q * 3 + (c9 % 3)] = s;
+        }
+        return;
+    }
     if (pl.b <= 32) {
         // Few chunks: one thread per (particle, component), chunks in order.
         for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;

@@ -134,6 +134,27 @@ __host__ __device__ inline Plan make_plan(int64_t m, const PlanParams &q)
     return best;
 }
 
+// Independent clusters in one context (nc == 0: a single system).  Particles of
+// cluster c are [cl_off[c], cl_off[c+1]); its j-records occupy the 256-aligned
+// range [rec_off[c], rec_off[c+1]) (zero-mass padding at the end), so every
+// j-tile of a cluster starts on a tile boundary.  The per-step arrays form the
+// work list written by the batch planning kernel.
+struct BatchView {
+    int32_t nc;
+    const int64_t *cl_off;   // [nc+1] particle offsets
+    const int64_t *rec_off;  // [nc+1] record offsets (multiples of 256)
+    const int32_t *rmap;     // [n] record index of each particle
+    const int32_t *cl_of;    // [n] cluster of each particle
+    int64_t *a_off;          // [nc+1] first position of each cluster in the active list
+    int64_t *item_off;       // [nc+1] first work item of each cluster
+    int64_t *part_off;       // [nc+1] first partial-sum row of each cluster
+    int32_t *tpi_c;          // [nc] threads per i-particle
+    int32_t *b_c;            // [nc] j-chunks
+    int64_t *tps;            // [1] tiles per j-chunk
+};
+
+constexpr int kBatchTpsMax = 64;   // tiles per j-chunk considered by the batch planner
+
 struct EvalArgs {
     Records rec;
     int64_t npad;
@@ -147,6 +168,7 @@ struct EvalArgs {
     int guard;               // eps == 0: skip r^2 == 0 pairs
     uint32_t tx_extra;       // testing: bytes expected per tile beyond those copied (0 normally)
     int32_t *err;
+    BatchView bv;            // clusters (bv.nc == 0: single system)
 };
 
 // Planner inputs of one precision (hg_eval.cu): tiles, tile size, i per thread,

@@ -176,9 +176,9 @@ __global__ void __launch_bounds__(kNBThreads) k_nb_count(const double *tend, int
             sc->m = tot;
             sc->t_cur = t_next;
             sc->done = 0;
-            if (count_step) {
+            if (count_step) {   // 1: count the step and m n interactions; 2: the step only
                 sc->steps += 1;
-                sc->interactions += tot * n;
+                if (count_step == 1) sc->interactions += tot * n;
             }
         } else {
             sc->m = 0;
@@ -278,11 +278,16 @@ __device__ __forceinline__ double f2d(float f)
 
 template <bool MIXED>
 __global__ void k_predict(const State st, const Records rec, int64_t n, int64_t npad, const double *t_dev,
-                          double t_host, const int64_t *m_dev)
+                          double t_host, const int64_t *m_dev, const int32_t *rmap)
 {
     if (m_dev && *m_dev <= 0) return;
     const double tt = t_dev ? *t_dev : t_host;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npad; i += (int64_t)gridDim.x * blockDim.x) {
+    // Single system: record i is particle i (padding beyond n).  Clusters:
+    // particle i goes to record rmap[i]; padding slots were written at set-up.
+    const int64_t count = rmap ? n : npad;
+    for (int64_t ii = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ii < count; ii += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = ii;
+        const int64_t r = rmap ? (int64_t)rmap[ii] : ii;
         if (MIXED) {
             float4 r0, r1, r2;
             float r3;
@@ -317,10 +322,10 @@ __global__ void k_predict(const State st, const Records rec, int64_t n, int64_t 
                 r2 = r1;
                 r3 = 0.f;
             }
-            static_cast<float4 *>(rec.p[0])[i] = r0;
-            static_cast<float4 *>(rec.p[1])[i] = r1;
-            static_cast<float4 *>(rec.p[2])[i] = r2;
-            static_cast<float *>(rec.p[3])[i] = r3;
+            static_cast<float4 *>(rec.p[0])[r] = r0;
+            static_cast<float4 *>(rec.p[1])[r] = r1;
+            static_cast<float4 *>(rec.p[2])[r] = r2;
+            static_cast<float *>(rec.p[3])[r] = r3;
         } else {
             double2 q0, q1, q2, q3, q4;
             if (i < n) {
@@ -335,11 +340,11 @@ __global__ void k_predict(const State st, const Records rec, int64_t n, int64_t 
                 q1 = make_double2(kPadCoord, 0.0);
                 q2 = q3 = q4 = make_double2(0.0, 0.0);
             }
-            static_cast<double2 *>(rec.p[0])[i] = q0;
-            static_cast<double2 *>(rec.p[1])[i] = q1;
-            static_cast<double2 *>(rec.p[2])[i] = q2;
-            static_cast<double2 *>(rec.p[3])[i] = q3;
-            static_cast<double2 *>(rec.p[4])[i] = q4;
+            static_cast<double2 *>(rec.p[0])[r] = q0;
+            static_cast<double2 *>(rec.p[1])[r] = q1;
+            static_cast<double2 *>(rec.p[2])[r] = q2;
+            static_cast<double2 *>(rec.p[3])[r] = q3;
+            static_cast<double2 *>(rec.p[4])[r] = q4;
         }
     }
 }
@@ -562,6 +567,24 @@ __global__ void __launch_bounds__(kPotThreads) k_potential(const double *xe, con
     if (i < n) phi_part[blockIdx.y * n + i] = phi;
 }
 
+// Independent clusters: phi_i sums over the other particles of i's own cluster
+// only (FP64 pairs, read from global memory; cluster sizes are modest).
+__global__ void k_potential_clusters(const double *xe, const double *mass, const int32_t *cl_of,
+                                     const int64_t *cl_off, int64_t n, double eps2, double *phi)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = cl_of[i];
+        const double xi = xe[3 * i], yi = xe[3 * i + 1], zi = xe[3 * i + 2];
+        double s = 0.0;
+        for (int64_t j = cl_off[c]; j < cl_off[c + 1]; ++j) {
+            const double dx = xe[3 * j] - xi, dy = xe[3 * j + 1] - yi, dz = xe[3 * j + 2] - zi;
+            const double r2 = fma(dz, dz, fma(dy, dy, fma(dx, dx, eps2)));
+            s += (j == i) ? 0.0 : mass[j] * rsqrt(r2);
+        }
+        phi[i] = s;
+    }
+}
+
 __global__ void k_energy_sum(const double *mass, const double *ve, const double *phi_part, int64_t n, int nsplit,
                              double *part2)
 {
@@ -664,6 +687,172 @@ __global__ void k_check_correct(const State st, const int32_t *given, const int3
     }
 }
 
+// ------------------------------------------------------------------------
+// Work list of one evaluation over independent clusters (one CTA).  For each
+// cluster: its range of the (ascending) active list by binary search, threads
+// per i-particle from its active count, j-chunks of tps tiles over its own
+// records; tps is common: the largest power of two up to 64 that still gives
+// at least two items per resident CTA (smaller tps only if the partial-sum
+// capacity allows).  Exclusive scans give each cluster's first work item and
+// first partial-sum row.
+// ------------------------------------------------------------------------
+constexpr int kPlanThreads = 1024;
+constexpr int kTpsCand = 7;   // tps = 1, 2, ..., 64
+
+__device__ void block_exscan_i64(int64_t v, int64_t *sh, int64_t &excl, int64_t &total)
+{
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    int64_t incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (l >= o) incl += u;
+    }
+    __syncthreads();
+    if (l == 31) sh[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const int64_t x = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0;
+        int64_t xi = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t u = __shfl_up_sync(0xffffffffu, xi, o);
+            if (l >= o) xi += u;
+        }
+        sh[l] = xi - x;
+        if (l == 31) sh[32] = xi;
+    }
+    __syncthreads();
+    excl = sh[w] + incl - v;
+    total = sh[32];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kPlanThreads) k_batch_plan(const int32_t *idx, const int64_t *m_dev, int64_t m_host,
+                                                             BatchView bv, int tj, int ipt, int grid, int64_t pcap,
+                                                             DevScalars *count)
+{
+    __shared__ int64_t sh[33];
+    __shared__ int64_t s_tps;
+    const int64_t m = m_dev ? *m_dev : m_host;
+    if (m <= 0) return;
+    const int nc = bv.nc;
+    for (int c = threadIdx.x; c <= nc; c += blockDim.x) {
+        if (c == nc) {
+            bv.a_off[nc] = m;
+            continue;
+        }
+        const int64_t key = bv.cl_off[c];
+        int64_t lo = 0, hi = m;   // first position with idx >= key
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (idx[mid] < key) lo = mid + 1; else hi = mid;
+        }
+        bv.a_off[c] = lo;
+    }
+    __syncthreads();
+    // This thread's clusters [c0, c1): active counts and tiles.
+    const int per = (nc + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int c0 = threadIdx.x * per, c1 = (c0 + per < nc) ? c0 + per : nc;
+    int64_t items[kTpsCand], parts[kTpsCand];
+    for (int k = 0; k < kTpsCand; ++k) items[k] = parts[k] = 0;
+    for (int c = c0; c < c1; ++c) {
+        const int64_t mc = bv.a_off[c + 1] - bv.a_off[c];
+        if (mc == 0) continue;
+        int tpi = 1;
+        const int64_t want = (int64_t)kEvalThreads * ipt / mc;
+        while (tpi * 2 <= want && tpi < kMaxTPI) tpi *= 2;
+        const int64_t ti = kEvalThreads / tpi * ipt;
+        const int64_t nit = (mc + ti - 1) / ti;
+        const int64_t ntc = (bv.rec_off[c + 1] - bv.rec_off[c]) / tj;
+        for (int k = 0; k < kTpsCand; ++k) {
+            const int64_t b = (ntc + (1 << k) - 1) >> k;
+            items[k] += nit * b;
+            parts[k] += b * mc;
+        }
+    }
+    for (int k = 0; k < kTpsCand; ++k) {
+        int64_t e, t;
+        block_exscan_i64(items[k], sh, e, t);
+        items[k] = t;
+        block_exscan_i64(parts[k], sh, e, t);
+        parts[k] = t;
+    }
+    if (threadIdx.x == 0) {
+        int pick = -1;
+        for (int k = kTpsCand - 1; k >= 0 && pick < 0; --k)
+            if (parts[k] <= pcap && items[k] >= 2 * (int64_t)grid) pick = k;
+        for (int k = 0; k < kTpsCand && pick < 0; ++k)
+            if (parts[k] <= pcap) pick = k;
+        if (pick < 0) pick = kTpsCand - 1;
+        s_tps = (int64_t)1 << pick;
+        *bv.tps = s_tps;
+    }
+    __syncthreads();
+    const int64_t tps = s_tps;
+    int64_t my_items = 0, my_parts = 0;
+    for (int c = c0; c < c1; ++c) {
+        const int64_t mc = bv.a_off[c + 1] - bv.a_off[c];
+        int tpi = 1;
+        if (mc > 0) {
+            const int64_t want = (int64_t)kEvalThreads * ipt / mc;
+            while (tpi * 2 <= want && tpi < kMaxTPI) tpi *= 2;
+        }
+        const int64_t ti = kEvalThreads / tpi * ipt;
+        const int64_t nit = (mc + ti - 1) / ti;
+        const int64_t ntc = (bv.rec_off[c + 1] - bv.rec_off[c]) / tj;
+        const int64_t b = (ntc + tps - 1) / tps;
+        bv.tpi_c[c] = tpi;
+        bv.b_c[c] = (int32_t)b;
+        my_items += nit * b;
+        my_parts += b * mc;
+    }
+    int64_t ie, it, pe, pt;
+    block_exscan_i64(my_items, sh, ie, it);
+    block_exscan_i64(my_parts, sh, pe, pt);
+    if (count) {   // pair evaluations of this block step: sum over clusters of m_c N_c
+        int64_t my_pairs = 0;
+        for (int c = c0; c < c1; ++c)
+            my_pairs += (bv.a_off[c + 1] - bv.a_off[c]) * (bv.cl_off[c + 1] - bv.cl_off[c]);
+        int64_t e, tot;
+        block_exscan_i64(my_pairs, sh, e, tot);
+        if (threadIdx.x == 0) count->interactions += tot;
+    }
+    for (int c = c0; c < c1; ++c) {
+        const int64_t mc = bv.a_off[c + 1] - bv.a_off[c];
+        const int64_t ti = kEvalThreads / bv.tpi_c[c] * ipt;
+        const int64_t nit = (mc + ti - 1) / ti;
+        bv.item_off[c] = ie;
+        bv.part_off[c] = pe;
+        ie += nit * bv.b_c[c];
+        pe += (int64_t)bv.b_c[c] * mc;
+    }
+    if (threadIdx.x == 0) {
+        bv.item_off[nc] = it;
+        bv.part_off[nc] = pt;
+    }
+}
+
+// Zero-mass padding records far away in every slot (before the first prediction
+// of a cluster context, whose particles do not cover all record slots).
+template <bool MIXED>
+__global__ void k_pad_records(Records rec, int64_t npad)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npad; i += (int64_t)gridDim.x * blockDim.x) {
+        if (MIXED) {
+            const float far = (float)kPadCoord;
+            static_cast<float4 *>(rec.p[0])[i] = make_float4(far, far, far, 0.f);
+            static_cast<float4 *>(rec.p[1])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            static_cast<float4 *>(rec.p[2])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            static_cast<float *>(rec.p[3])[i] = 0.f;
+        } else {
+            static_cast<double2 *>(rec.p[0])[i] = make_double2(kPadCoord, kPadCoord);
+            static_cast<double2 *>(rec.p[1])[i] = make_double2(kPadCoord, 0.0);
+            static_cast<double2 *>(rec.p[2])[i] = make_double2(0.0, 0.0);
+            static_cast<double2 *>(rec.p[3])[i] = make_double2(0.0, 0.0);
+            static_cast<double2 *>(rec.p[4])[i] = make_double2(0.0, 0.0);
+        }
+    }
+}
+
 // tend = t + dt for every particle (after the state is replaced).
 __global__ void k_tend(State st, int64_t n)
 {
@@ -703,13 +892,30 @@ cudaError_t launch_tend(const State &st, int64_t n, cudaStream_t s)
 }
 
 cudaError_t launch_predict(bool mixed, const State &st, const Records &rec, int64_t n, int64_t npad,
-                           const double *t_dev, double t_host, const int64_t *m_dev, cudaStream_t s)
+                           const double *t_dev, double t_host, const int64_t *m_dev, const int32_t *rmap,
+                           cudaStream_t s)
 {
-    const int g = grid_for(npad, 64, 1 << 20);   // small CTAs: even spread of the FP64 work
+    const int g = grid_for(rmap ? n : npad, 64, 1 << 20);   // small CTAs: even spread of the FP64 work
     if (mixed)
-        k_predict<true><<<g, 64, 0, s>>>(st, rec, n, npad, t_dev, t_host, m_dev);
+        k_predict<true><<<g, 64, 0, s>>>(st, rec, n, npad, t_dev, t_host, m_dev, rmap);
     else
-        k_predict<false><<<g, 64, 0, s>>>(st, rec, n, npad, t_dev, t_host, m_dev);
+        k_predict<false><<<g, 64, 0, s>>>(st, rec, n, npad, t_dev, t_host, m_dev, rmap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pad_records(bool mixed, const Records &rec, int64_t npad, cudaStream_t s)
+{
+    if (mixed)
+        k_pad_records<true><<<grid_for(npad, 256, 1 << 20), 256, 0, s>>>(rec, npad);
+    else
+        k_pad_records<false><<<grid_for(npad, 256, 1 << 20), 256, 0, s>>>(rec, npad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_plan(const int32_t *idx, const int64_t *m_dev, int64_t m_host, const BatchView &bv, int tj,
+                              int ipt, int grid, int64_t pcap, DevScalars *count, cudaStream_t s)
+{
+    k_batch_plan<<<1, kPlanThreads, 0, s>>>(idx, m_dev, m_host, bv, tj, ipt, grid, pcap, count);
     return cudaGetLastError();
 }
 
@@ -739,16 +945,22 @@ int energy_splits(int64_t n, int num_sms)
 }
 
 cudaError_t launch_energy(bool mixed, const State &st, int64_t n, double t, double eps2, double *xe, double *ve,
-                          double *phi_part, int nsplit, double *part2, int g2, double *out2, cudaStream_t s)
+                          double *phi_part, int nsplit, double *part2, int g2, double *out2, const BatchView &bv,
+                          cudaStream_t s)
 {
     k_predict_xv<<<grid_for(n, 256, 1 << 20), 256, 0, s>>>(st, n, t, xe, ve);
     int64_t jchunk = (n + nsplit - 1) / nsplit;
     jchunk = (jchunk + kPotThreads - 1) / kPotThreads * kPotThreads;
     dim3 grid((unsigned)((n + kPotThreads - 1) / kPotThreads), (unsigned)nsplit);
-    if (mixed)
+    if (bv.nc > 0) {
+        k_potential_clusters<<<grid_for(n, 128, 1 << 20), 128, 0, s>>>(xe, st.mass, bv.cl_of, bv.cl_off, n, eps2,
+                                                                        phi_part);
+        nsplit = 1;
+    } else if (mixed) {
         k_potential<true><<<grid, kPotThreads, 0, s>>>(xe, st.mass, n, jchunk, eps2, phi_part);
-    else
+    } else {
         k_potential<false><<<grid, kPotThreads, 0, s>>>(xe, st.mass, n, jchunk, eps2, phi_part);
+    }
     k_energy_sum<<<g2, 256, 0, s>>>(st.mass, ve, phi_part, n, nsplit, part2);
     k_energy_final<<<1, 32, 0, s>>>(part2, g2, out2);
     return cudaGetLastError();

@@ -17,15 +17,24 @@ cudaError_t launch_next_block(const State &st, int64_t n, double *part, int32_t 
                               DevScalars *sc, int count_step, const PlanParams &pq, cudaStream_t s);
 // tend = t + dt after the state was replaced.
 cudaError_t launch_tend(const State &st, int64_t n, cudaStream_t s);
+// rmap: record of each particle (clusters), or nullptr (record i = particle i).
 cudaError_t launch_predict(bool mixed, const State &st, const Records &rec, int64_t n, int64_t npad,
-                           const double *t_dev, double t_host, const int64_t *m_dev, cudaStream_t s);
+                           const double *t_dev, double t_host, const int64_t *m_dev, const int32_t *rmap,
+                           cudaStream_t s);
+// Padding in every record slot (cluster contexts, before the first prediction).
+cudaError_t launch_pad_records(bool mixed, const Records &rec, int64_t npad, cudaStream_t s);
+// Work list of one evaluation over clusters (sizes on the device or host);
+// count != nullptr adds the step's pair evaluations to count->interactions.
+cudaError_t launch_batch_plan(const int32_t *idx, const int64_t *m_dev, int64_t m_host, const BatchView &bv, int tj,
+                              int ipt, int grid, int64_t pcap, DevScalars *count, cudaStream_t s);
 cudaError_t launch_start(const State &st, int64_t n, const double *ra, const double *rj, const double *rs,
                          const StepParams &sp, cudaStream_t s);
 cudaError_t launch_correct(const State &st, const int32_t *idx, const int64_t *m_dev, int64_t m_host, int64_t n_max,
                            const double *ra, const double *rj, const double *rs, const StepParams &sp, cudaStream_t s);
 int energy_splits(int64_t n, int num_sms);
 cudaError_t launch_energy(bool mixed, const State &st, int64_t n, double t, double eps2, double *xe, double *ve,
-                          double *phi_part, int nsplit, double *part2, int g2, double *out2, cudaStream_t s);
+                          double *phi_part, int nsplit, double *part2, int g2, double *out2, const BatchView &bv,
+                          cudaStream_t s);
 cudaError_t launch_validate_init(const double *mass, const double *x, const double *v, int64_t n, int32_t *flag,
                                  cudaStream_t s);
 cudaError_t launch_validate_state(const State &st, int64_t n, double dt_min, double dt_max, int32_t *flag,
