@@ -119,6 +119,9 @@ StepParams step_params(const hg_ctx *c)
     p.eta_init = c->opts.eta_init;
     p.dt_min = c->opts.dt_min;
     p.dt_max = c->opts.dt_max;
+    // FP32 pair arithmetic resolves accelerations to ~1e-7 relative; a change
+    // below 3e-6 |a| carries no usable higher-derivative information.
+    p.noise_rel = c->mixed ? 3e-6 : 0.0;
     return p;
 }
 
@@ -214,8 +217,11 @@ int enqueue_block_step(hg_ctx *c, cudaStream_t s, const cudaEvent_t *ev)
                                  c->bv.nc > 0 ? 2 : 1, c->pp, s));
     if (c->bv.nc > 0) HG_CUDA(c, batch_plan(c, &c->d_sc->m, 0, s));
     if (ev) HG_CUDA(c, record_external(ev[1], s));
-    HG_CUDA(c, launch_predict(c->mixed, c->st, c->rec, c->n, c->npad, &c->d_sc->t_cur, 0.0, &c->d_sc->m, rmap_of(c),
-                              s));
+    if (c->bv.nc > 0)
+        HG_CUDA(c, launch_predict_clusters(c->mixed, c->st, c->rec, c->n, c->bv, &c->d_sc->t_cur, &c->d_sc->m, s));
+    else
+        HG_CUDA(c, launch_predict(c->mixed, c->st, c->rec, c->n, c->npad, &c->d_sc->t_cur, 0.0, &c->d_sc->m, nullptr,
+                                  s));
     if (ev) HG_CUDA(c, record_external(ev[2], s));
     EvalArgs a = eval_args(c, &c->d_sc->m, 0);
     HG_CUDA(c, launch_eval(c->mixed, a, c->egrid, s));
@@ -378,10 +384,12 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
         bv.a_off = dalloc<int64_t>(c, nc + 1);
         bv.item_off = dalloc<int64_t>(c, nc + 1);
         bv.part_off = dalloc<int64_t>(c, nc + 1);
+        bv.pred_off = dalloc<int64_t>(c, nc + 1);
         bv.tpi_c = dalloc<int32_t>(c, nc);
         bv.b_c = dalloc<int32_t>(c, nc);
         bv.tps = dalloc<int64_t>(c, 1);
-        if (!clo || !ro || !rm || !co || !bv.a_off || !bv.item_off || !bv.part_off || !bv.tpi_c || !bv.b_c || !bv.tps)
+        if (!clo || !ro || !rm || !co || !bv.a_off || !bv.item_off || !bv.part_off || !bv.pred_off || !bv.tpi_c ||
+            !bv.b_c || !bv.tps)
             return fail(c, HG_ENOMEM, "device allocation failed");
         HG_CUDA(c, cudaMemcpy(clo, c->cl_off_host.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
         HG_CUDA(c, cudaMemcpy(ro, rec_off.data(), (nc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));

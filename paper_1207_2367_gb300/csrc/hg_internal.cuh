@@ -148,6 +148,7 @@ struct BatchView {
     int64_t *a_off;          // [nc+1] first position of each cluster in the active list
     int64_t *item_off;       // [nc+1] first work item of each cluster
     int64_t *part_off;       // [nc+1] first partial-sum row of each cluster
+    int64_t *pred_off;       // [nc+1] prefix of the sizes of clusters with active particles
     int32_t *tpi_c;          // [nc] threads per i-particle
     int32_t *b_c;            // [nc] j-chunks
     int64_t *tps;            // [1] tiles per j-chunk

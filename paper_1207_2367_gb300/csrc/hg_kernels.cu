@@ -276,18 +276,12 @@ __device__ __forceinline__ double f2d(float f)
     return __longlong_as_double((long long)(e == 0u ? sign : (sign | mag)));
 }
 
+// Record r from particle i predicted to time tt (i >= n: a padding record).
 template <bool MIXED>
-__global__ void k_predict(const State st, const Records rec, int64_t n, int64_t npad, const double *t_dev,
-                          double t_host, const int64_t *m_dev, const int32_t *rmap)
+__device__ __forceinline__ void predict_record(const State &st, const Records &rec, int64_t i, int64_t n, int64_t r,
+                                               double tt)
 {
-    if (m_dev && *m_dev <= 0) return;
-    const double tt = t_dev ? *t_dev : t_host;
-    // Single system: record i is particle i (padding beyond n).  Clusters:
-    // particle i goes to record rmap[i]; padding slots were written at set-up.
-    const int64_t count = rmap ? n : npad;
-    for (int64_t ii = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ii < count; ii += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = ii;
-        const int64_t r = rmap ? (int64_t)rmap[ii] : ii;
+    {
         if (MIXED) {
             float4 r0, r1, r2;
             float r3;
@@ -346,6 +340,40 @@ __global__ void k_predict(const State st, const Records rec, int64_t n, int64_t 
             static_cast<double2 *>(rec.p[3])[r] = q3;
             static_cast<double2 *>(rec.p[4])[r] = q4;
         }
+    }
+}
+
+// Single system: record i is particle i (padding beyond n).  Clusters:
+// particle i goes to record rmap[i]; padding slots were written at set-up.
+template <bool MIXED>
+__global__ void k_predict(const State st, const Records rec, int64_t n, int64_t npad, const double *t_dev,
+                          double t_host, const int64_t *m_dev, const int32_t *rmap)
+{
+    if (m_dev && *m_dev <= 0) return;
+    const double tt = t_dev ? *t_dev : t_host;
+    const int64_t count = rmap ? n : npad;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        predict_record<MIXED>(st, rec, i, n, rmap ? (int64_t)rmap[i] : i, tt);
+}
+
+// Clusters, in a block step: only the clusters with active particles need
+// predicted data.  Work index w in [0, pred_off[nc]) is particle
+// cl_off[c] + (w - pred_off[c]) of the cluster c whose range holds w.
+template <bool MIXED>
+__global__ void k_predict_clusters(const State st, const Records rec, int64_t n, BatchView bv, const double *t_dev,
+                                   const int64_t *m_dev)
+{
+    if (*m_dev <= 0) return;
+    const double tt = *t_dev;
+    const int64_t total = bv.pred_off[bv.nc];
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = bv.nc - 1;   // last cluster with pred_off[c] <= w
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (bv.pred_off[mid] <= w) lo = mid; else hi = mid - 1;
+        }
+        const int64_t i = bv.cl_off[lo] + (w - bv.pred_off[lo]);
+        predict_record<MIXED>(st, rec, i, n, bv.rmap[i], tt);
     }
 }
 
@@ -434,7 +462,7 @@ __global__ void k_start(State st, int64_t n, const double *ra, const double *rj,
 // the new a, jerk, snap and crackle), and crackle, pop and a^(5) from the
 // degree-5 interpolant through a, jerk, snap at both ends of the step.
 __device__ __forceinline__ void correct_component(const State &st, int64_t i, int k, double h, double a1, double j1,
-                                                  double s1, double &c3, double &c4, double &c5)
+                                                  double s1, double &c3, double &c4, double &c5, double &Ak)
 {
     const double hh = h / 2.0, h2 = h * h / 10.0, h3 = h * h * h / 120.0;
     // h is a power of two: its reciprocal powers are exact.
@@ -449,6 +477,7 @@ __device__ __forceinline__ void correct_component(const State &st, int64_t i, in
     c3 = (60.0 * A - 36.0 * J + 9.0 * S) * ih3;
     c4 = (360.0 * A - 192.0 * J + 36.0 * S) * ih4;
     c5 = (720.0 * A - 360.0 * J + 60.0 * S) * ih5;
+    Ak = A;
     st.x[q] = x1;
     st.v[q] = v1;
     st.a[q] = a1;
@@ -458,11 +487,16 @@ __device__ __forceinline__ void correct_component(const State &st, int64_t i, in
 }
 
 // New time and p = 6 step of particle i from d = a^(0..5) at the step's end.
+// A: the acceleration change left after a0 + j0 h + s0 h^2/2.  Below the noise
+// floor of the evaluation (sp.noise_rel |a1|) the interpolated derivatives are
+// noise and the criterion is not allowed to shrink the step.
 __device__ __forceinline__ void finish_step(const State &st, int64_t i, double h, const double (*d)[3],
-                                            const StepParams &sp)
+                                            const double *A, const StepParams &sp)
 {
     const double t1 = st.t[i] + h;
-    const double dt1 = block_dt(criterion(sp.eta, 6, d), h, t1, sp.dt_min, sp.dt_max);
+    double crit = criterion(sp.eta, 6, d);
+    if (sp.noise_rel > 0.0 && norm3(A) < sp.noise_rel * norm3(d[0])) crit = INFINITY;
+    const double dt1 = block_dt(crit, h, t1, sp.dt_min, sp.dt_max);
     st.t[i] = t1;
     st.dt[i] = dt1;
     st.tend[i] = t1 + dt1;
@@ -475,11 +509,11 @@ __global__ void k_correct(State st, const int32_t *idx, const int64_t *m_dev, in
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = idx[q];
         const double h = st.dt[i];
-        double d[6][3];
+        double d[6][3], A[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             double c3, c4, c5;
-            correct_component(st, i, k, h, ra[3 * q + k], rj[3 * q + k], rs[3 * q + k], c3, c4, c5);
+            correct_component(st, i, k, h, ra[3 * q + k], rj[3 * q + k], rs[3 * q + k], c3, c4, c5, A[k]);
             d[0][k] = ra[3 * q + k];
             d[1][k] = rj[3 * q + k];
             d[2][k] = rs[3 * q + k];
@@ -487,7 +521,7 @@ __global__ void k_correct(State st, const int32_t *idx, const int64_t *m_dev, in
             d[4][k] = c4;
             d[5][k] = c5;
         }
-        finish_step(st, i, h, d, sp);
+        finish_step(st, i, h, d, A, sp);
     }
 }
 
@@ -805,7 +839,15 @@ __global__ void __launch_bounds__(kPlanThreads) k_batch_plan(const int32_t *idx,
         my_items += nit * b;
         my_parts += b * mc;
     }
-    int64_t ie, it, pe, pt;
+    int64_t ie, it, pe, pt, we, wt, my_pred = 0;
+    for (int c = c0; c < c1; ++c)
+        if (bv.a_off[c + 1] > bv.a_off[c]) my_pred += bv.cl_off[c + 1] - bv.cl_off[c];
+    block_exscan_i64(my_pred, sh, we, wt);
+    for (int c = c0; c < c1; ++c) {
+        bv.pred_off[c] = we;
+        if (bv.a_off[c + 1] > bv.a_off[c]) we += bv.cl_off[c + 1] - bv.cl_off[c];
+    }
+    if (threadIdx.x == 0) bv.pred_off[nc] = wt;
     block_exscan_i64(my_items, sh, ie, it);
     block_exscan_i64(my_parts, sh, pe, pt);
     if (count) {   // pair evaluations of this block step: sum over clusters of m_c N_c
@@ -900,6 +942,17 @@ cudaError_t launch_predict(bool mixed, const State &st, const Records &rec, int6
         k_predict<true><<<g, 64, 0, s>>>(st, rec, n, npad, t_dev, t_host, m_dev, rmap);
     else
         k_predict<false><<<g, 64, 0, s>>>(st, rec, n, npad, t_dev, t_host, m_dev, rmap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_predict_clusters(bool mixed, const State &st, const Records &rec, int64_t n, const BatchView &bv,
+                                    const double *t_dev, const int64_t *m_dev, cudaStream_t s)
+{
+    const int g = grid_for(n, 64, 1 << 20);
+    if (mixed)
+        k_predict_clusters<true><<<g, 64, 0, s>>>(st, rec, n, bv, t_dev, m_dev);
+    else
+        k_predict_clusters<false><<<g, 64, 0, s>>>(st, rec, n, bv, t_dev, m_dev);
     return cudaGetLastError();
 }
 

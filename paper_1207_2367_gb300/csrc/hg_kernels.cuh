@@ -7,6 +7,10 @@ namespace hg {
 
 struct StepParams {
     double eta, eta_init, dt_min, dt_max;
+    // Relative noise floor of the evaluated acceleration (0: exact enough, FP64).
+    // When |a1 - a0 - j0 h - s0 h^2/2| < noise_rel |a1| the interpolated crackle,
+    // pop and 5th derivative are unresolved: the criterion then does not shrink the step.
+    double noise_rel;
 };
 
 constexpr int64_t kNBChunk = 2048;   // particles per CTA in the next-block passes
@@ -21,6 +25,10 @@ cudaError_t launch_tend(const State &st, int64_t n, cudaStream_t s);
 cudaError_t launch_predict(bool mixed, const State &st, const Records &rec, int64_t n, int64_t npad,
                            const double *t_dev, double t_host, const int64_t *m_dev, const int32_t *rmap,
                            cudaStream_t s);
+// Clusters in a block step: predict only the clusters with active particles
+// (after the batch planning kernel of that step).
+cudaError_t launch_predict_clusters(bool mixed, const State &st, const Records &rec, int64_t n, const BatchView &bv,
+                                    const double *t_dev, const int64_t *m_dev, cudaStream_t s);
 // Padding in every record slot (cluster contexts, before the first prediction).
 cudaError_t launch_pad_records(bool mixed, const Records &rec, int64_t npad, cudaStream_t s);
 // Work list of one evaluation over clusters (sizes on the device or host);
