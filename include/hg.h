@@ -214,6 +214,55 @@ int hg_evaluate_static(int64_t n, const double *mass, const double *pos, const d
                        double eps, int32_t precision, const int32_t *idx, int64_t m, double *acc, double *jerk,
                        double *snap, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Autotuning of the evaluation's launch plan (the paper's "Bfactor", Sect. 3:
+ * how the m active particles and the n j-particles are spread over the GPU).
+ * Block sizes are grouped in HG_TUNE_BUCKETS buckets, bucket k holding
+ * 2^k <= m < 2^(k+1).  For each bucket the table holds -1 (use the built-in
+ * cost model) or a measured choice:
+ *  - one system: a plan index c in [0, 224): 2^(c / 32) threads share one
+ *    i-particle (the i-tile is 256 / 2^(c/32) particles mixed, 128 / 2^(c/32)
+ *    FP64) and each j-chunk holds T[c % 32] j-tiles (256 records mixed, 128
+ *    FP64), T = {1, 2, ..., 16, 20, 24, 32, 40, 48, 64, 96, 128, 192, 256,
+ *    384, 512, 1024, 2048, 4096, 8192};
+ *  - clusters (hg_init_batch): a code w + 8 (s + 1), w in [0, 6], s in
+ *    {-1, 0, 1}: the j-split is the largest one leaving at least 2^w work items
+ *    per resident CTA, and each cluster's threads per i-particle are 2^s times
+ *    the number that fills one CTA with its active particles.
+ * A plan that is not admissible for the actual m (partial-sum capacity, or the
+ * opts.tpi / opts.jsplit overrides) falls back to the cost model.
+ * ------------------------------------------------------------------------ */
+#define HG_TUNE_BUCKETS 32
+
+/* One bucket measured by hg_tune. */
+typedef struct hg_tune_entry {
+    int64_t m;           /* block size timed: the m particles with the smallest steps */
+    int32_t bucket;      /* floor(log2 m) */
+    int32_t candidates;  /* plans timed */
+    int32_t model;       /* the cost model's choice, in table encoding */
+    int32_t chosen;      /* value stored in the table (-1: the cost model was kept) */
+    double model_us;     /* device time of evaluation + reduction with the model's plan, us */
+    double best_us;      /* the same for the stored choice (model_us when chosen == -1) */
+} hg_tune_entry;
+
+/* Measure, for every bucket whose m is at most m_max (0: n; the m of bucket k is
+ * 2^k for k = 0 and floor(1.5 * 2^k) clamped to n above), the cost model's plan
+ * and its cheapest rivals on the context's current predicted data, with CUDA
+ * events on the context's stream, each plan launched reps times (0: automatic)
+ * after one warm-up; store a rival only if it is at least 3% faster.  The
+ * integration state is unchanged, a pending hg_evaluate is dropped and the
+ * captured graphs are rebuilt on their next use.  report (capacity cap, may be
+ * NULL) receives one entry per bucket measured; *n_out their number.
+ * Errors: HG_EINVAL, HG_ECUDA, HG_ETIMEOUT.  Synchronizes. */
+int hg_tune(hg_ctx *ctx, int64_t m_max, int32_t reps, hg_tune_entry *report, int32_t cap, int32_t *n_out);
+
+/* Copy the tuning table out / replace it (HG_TUNE_BUCKETS int16 values, host
+ * memory; -1 entries use the cost model).  hg_set_tuning checks every value for
+ * the context's kind (HG_EINVAL otherwise), so a table saved from one context
+ * can be given to another of the same precision and kind on the same GPU model. */
+int hg_get_tuning(hg_ctx *ctx, int16_t *table);
+int hg_set_tuning(hg_ctx *ctx, const int16_t *table);
+
 /* Release the context and its device memory.  NULL is allowed. */
 void hg_free(hg_ctx *ctx);
 

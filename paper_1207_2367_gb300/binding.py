@@ -50,6 +50,12 @@ class hg_profile(C.Structure):
     _fields_ = [("ms", C.c_double * 5), ("block_steps", C.c_int64)]
 
 
+class hg_tune_entry(C.Structure):
+    _fields_ = [("m", C.c_int64), ("bucket", C.c_int32), ("candidates", C.c_int32), ("model", C.c_int32),
+                ("chosen", C.c_int32), ("model_us", C.c_double), ("best_us", C.c_double)]
+
+
+HG_TUNE_BUCKETS = 32
 SECTIONS = ("next", "predict", "evaluate", "reduce", "correct")
 
 
@@ -94,8 +100,12 @@ def load(path: str | None = None):
         L.hg_free.restype = None
         L.hg_evaluate_static.argtypes = [I64, P, P, P, P, D, C.c_int32, I32P, I64, P, P, P, P]
         L.hg_evaluate_static.restype = C.c_int
+        L.hg_tune.argtypes = [P, I64, C.c_int32, C.POINTER(hg_tune_entry), C.c_int32, C.POINTER(C.c_int32)]
+        L.hg_get_tuning.argtypes = [P, C.POINTER(C.c_int16)]
+        L.hg_set_tuning.argtypes = [P, C.POINTER(C.c_int16)]
         for name in ("hg_init", "hg_next_block", "hg_predict", "hg_evaluate", "hg_correct", "hg_step",
-                     "hg_advance", "hg_energy", "hg_get_state", "hg_set_state", "hg_get_stats", "hg_get_profile"):
+                     "hg_advance", "hg_energy", "hg_get_state", "hg_set_state", "hg_get_stats", "hg_get_profile",
+                     "hg_tune", "hg_get_tuning", "hg_set_tuning"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -226,6 +236,28 @@ def hg_get_profile(ctx, reset=False):
     p = hg_profile()
     _check(ctx, load().hg_get_profile(ctx, C.byref(p), int(bool(reset))))
     return {"ms": dict(zip(SECTIONS, list(p.ms))), "block_steps": p.block_steps}
+
+
+def hg_tune(ctx, m_max=0, reps=0):
+    """Time the evaluation plans per block-size bucket; returns one dict per bucket measured."""
+    rep = (hg_tune_entry * HG_TUNE_BUCKETS)()
+    n = C.c_int32(0)
+    _check(ctx, load().hg_tune(ctx, int(m_max), int(reps), rep, HG_TUNE_BUCKETS, C.byref(n)))
+    keys = [f for f, _ in hg_tune_entry._fields_]
+    return [{k: getattr(rep[q], k) for k in keys} for q in range(n.value)]
+
+
+def hg_get_tuning(ctx):
+    t = np.empty(HG_TUNE_BUCKETS, dtype=np.int16)
+    _check(ctx, load().hg_get_tuning(ctx, t.ctypes.data_as(C.POINTER(C.c_int16))))
+    return t
+
+
+def hg_set_tuning(ctx, table):
+    t = np.ascontiguousarray(table, dtype=np.int16)
+    if t.shape != (HG_TUNE_BUCKETS,):
+        raise ValueError(f"the table holds {HG_TUNE_BUCKETS} values")
+    _check(ctx, load().hg_set_tuning(ctx, t.ctypes.data_as(C.POINTER(C.c_int16))))
 
 
 def hg_evaluate_static(mass, pos, vel, acc_pred, eps, precision, idx, m, acc, jerk, snap, stream=None):

@@ -6,6 +6,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -149,8 +150,7 @@ const int32_t *rmap_of(const hg_ctx *c) { return c->bv.nc > 0 ? c->bv.rmap : nul
 // Work list over clusters; in graph steps it also counts the step's pair evaluations.
 cudaError_t batch_plan(hg_ctx *c, const int64_t *m_dev, int64_t m_host, cudaStream_t s)
 {
-    return launch_batch_plan(c->d_idx, m_dev, m_host, c->bv, c->pp.tj, c->pp.i_per_thread, c->egrid, c->pcap,
-                             m_dev ? c->d_sc : nullptr, s);
+    return launch_batch_plan(c->d_idx, m_dev, m_host, c->bv, c->pp, m_dev ? c->d_sc : nullptr, s);
 }
 
 // Evaluation of the list in d_idx (host-known size m) into ra/rj/rs.
@@ -281,6 +281,20 @@ int replay(hg_ctx *c, bool many)
         }
     c->prof_steps += steps;
     return HG_OK;
+}
+
+// Captured graphs hold kernel arguments by value (list pointers, planner
+// inputs): drop them when those change; they are captured again on next use.
+void drop_graphs(hg_ctx *c)
+{
+    if (c->g_one) {
+        cudaGraphExecDestroy(c->g_one);
+        c->g_one = nullptr;
+    }
+    if (c->g_many) {
+        cudaGraphExecDestroy(c->g_many);
+        c->g_many = nullptr;
+    }
 }
 
 void invalidate(hg_ctx *c)
@@ -459,6 +473,155 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
     return HG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuning of the evaluation plan per block-size bucket.
+// ---------------------------------------------------------------------------
+constexpr int kTuneCand = 12;        // cheapest plans of the cost model timed per bucket
+constexpr double kTuneGain = 0.97;   // a rival is stored only if at least 3% faster
+constexpr double kTuneTargetUs = 2000.0;
+
+// Mean device time of `reps` evaluations + reductions of the list in d_idx with
+// the current planner inputs, after one warm-up (reps == 0: chosen from the
+// warm-up's time so that the timed launches take ~2 ms, 3..64).
+int time_eval(hg_ctx *c, int64_t m, int *reps, cudaEvent_t e0, cudaEvent_t e1, double *us)
+{
+    HG_CUDA(c, cudaEventRecord(e0, c->stream));
+    int rc = run_eval_host_m(c, m);
+    if (rc) return rc;
+    HG_CUDA(c, cudaEventRecord(e1, c->stream));
+    HG_CUDA(c, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    HG_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+    if (*reps <= 0) {
+        const double one = ms > 0.f ? 1000.0 * ms : 1.0;
+        *reps = (int)std::min(64.0, std::max(3.0, ceil(kTuneTargetUs / one)));
+    }
+    HG_CUDA(c, cudaEventRecord(e0, c->stream));
+    for (int r = 0; r < *reps; ++r)
+        if ((rc = run_eval_host_m(c, m)) != HG_OK) return rc;
+    HG_CUDA(c, cudaEventRecord(e1, c->stream));
+    HG_CUDA(c, cudaEventSynchronize(e1));
+    HG_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+    *us = 1000.0 * ms / *reps;
+    return HG_OK;
+}
+
+// Table values to time for a block of m: the cost model's choice first, then
+// its cheapest rivals (one system: distinct (tpi, b) plans, cheapest first, plus
+// the cheapest of every tpi; clusters: every batch code).
+std::vector<int> tune_candidates(const hg_ctx *c, int64_t m)
+{
+    std::vector<int> out;
+    if (c->bv.nc > 0) {
+        out.push_back(1 + 8 * 1);   // the untuned knobs w = 1, s = 0
+        for (int s = 0; s <= 2; ++s)
+            for (int w = 0; w <= kBatchWMax; ++w)
+                if (w + 8 * s != out[0]) out.push_back(w + 8 * s);
+        return out;
+    }
+    PlanParams q = c->pp;
+    for (int k = 0; k < kTuneBuckets; ++k) q.tuned[k] = -1;
+    struct Cand {
+        int64_t cost;
+        int c, tpi, b;
+    };
+    std::vector<Cand> all;
+    for (int k = 0; k < kPlanCandidates; ++k) {
+        Plan p;
+        const int64_t cost = plan_candidate(m, q, k, p);
+        if (cost < 0) continue;
+        bool dup = false;
+        for (const Cand &x : all) dup = dup || (x.tpi == p.tpi && x.b == p.b);
+        if (!dup) all.push_back(Cand{cost, k, p.tpi, p.b});
+    }
+    std::stable_sort(all.begin(), all.end(), [](const Cand &a, const Cand &b) { return a.cost < b.cost; });
+    std::vector<bool> take(all.size(), false);
+    for (size_t k = 0; k < all.size() && (int)k < kTuneCand; ++k) take[k] = true;
+    for (int t = 1; t <= kMaxTPI; t *= 2)
+        for (size_t k = 0; k < all.size(); ++k)
+            if (all[k].tpi == t) {
+                take[k] = true;
+                break;
+            }
+    for (size_t k = 0; k < all.size(); ++k)
+        if (take[k]) out.push_back(all[k].c);
+    return out;
+}
+
+int tune_impl(hg_ctx *c, int64_t m_max, int32_t reps_in, hg_tune_entry *report, int32_t cap, int32_t *n_out)
+{
+    const int64_t n = c->n;
+    if (m_max <= 0) {   // automatic: evaluations of up to ~2^32 (mixed) or 2^28 (FP64) pair interactions
+        const int64_t budget = c->mixed ? ((int64_t)1 << 32) : ((int64_t)1 << 28);
+        m_max = std::max<int64_t>(1, budget / n);
+    }
+    const int64_t mtop = std::min(m_max, n);
+    // Representative blocks: the particles with the smallest steps are the ones
+    // the block scheme makes active most often.
+    std::vector<double> dt((size_t)n);
+    HG_CUDA(c, cudaMemcpyAsync(dt.data(), c->st.dt, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    HG_CUDA(c, cudaStreamSynchronize(c->stream));
+    std::vector<int32_t> order((size_t)n);
+    for (int64_t i = 0; i < n; ++i) order[(size_t)i] = (int32_t)i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return dt[(size_t)a] < dt[(size_t)b]; });
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    HG_CUDA(c, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(c, HG_ECUDA, "cudaEventCreate failed");
+    }
+    drop_graphs(c);
+    invalidate(c);
+    int rc = HG_OK;
+    int32_t count = 0;
+    std::vector<int32_t> list;
+    for (int k = 0; k <= tune_bucket(mtop) && rc == HG_OK; ++k) {
+        const int64_t m = k == 0 ? 1 : std::min<int64_t>(mtop, (int64_t)3 << (k - 1));
+        list.assign(order.begin(), order.begin() + m);
+        std::sort(list.begin(), list.end());
+        if (cudaMemcpyAsync(c->d_idx, list.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            rc = fail(c, HG_ECUDA, "list upload failed");
+            break;
+        }
+        const std::vector<int> cand = tune_candidates(c, m);
+        int reps = reps_in;
+        double model_us = 0.0, best_us = 0.0;
+        int best = -1;
+        for (size_t q = 0; q < cand.size() && rc == HG_OK; ++q) {
+            c->pp.tuned[k] = q == 0 ? -1 : (int16_t)cand[q];   // q == 0: the cost model itself
+            double us = 0.0;
+            rc = time_eval(c, m, &reps, e0, e1, &us);
+            if (q == 0) {
+                model_us = best_us = us;
+            } else if (us < best_us) {
+                best_us = us;
+                best = cand[q];
+            }
+        }
+        if (rc) break;
+        const int chosen = (best >= 0 && best_us < kTuneGain * model_us) ? best : -1;
+        c->pp.tuned[k] = (int16_t)chosen;
+        if (report && count < cap) {
+            hg_tune_entry &e = report[count];
+            e.m = m;
+            e.bucket = k;
+            e.candidates = (int32_t)cand.size();
+            e.model = cand[0];
+            e.chosen = chosen;
+            e.model_us = model_us;
+            e.best_us = chosen >= 0 ? best_us : model_us;
+        }
+        ++count;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (n_out) *n_out = count;
+    return sync_scalars(c);
+}
+
 }  // namespace
 
 void hg::set_call_error(const char *msg) { g_init_err = msg; }
@@ -616,9 +779,7 @@ int hg_evaluate(hg_ctx *c, const int32_t *idx, int64_t m, double *acc, double *j
         c->d_idx = c->d_idx2;
         c->d_idx2 = t;
         c->cur_m = m;
-        // Graphs captured the old list pointer: rebuild them on next use.
-        if (c->g_one) { cudaGraphExecDestroy(c->g_one); c->g_one = nullptr; }
-        if (c->g_many) { cudaGraphExecDestroy(c->g_many); c->g_many = nullptr; }
+        drop_graphs(c);   // they captured the old list pointer
     }
     if (m > 0) {
         int rc = run_eval_host_m(c, m);
@@ -809,6 +970,41 @@ int hg_get_profile(hg_ctx *c, hg_profile *o, int reset)
         for (int q = 0; q < 5; ++q) c->prof_ms[q] = 0.0;
         c->prof_steps = 0;
     }
+    return HG_OK;
+}
+
+int hg_tune(hg_ctx *c, int64_t m_max, int32_t reps, hg_tune_entry *report, int32_t cap, int32_t *n_out)
+{
+    if (!c) return HG_EINVAL;
+    if (reps < 0 || reps > 1000) return fail(c, HG_EINVAL, "reps must be in [0, 1000]");
+    if (cap < 0 || (cap > 0 && !report)) return fail(c, HG_EINVAL, "report capacity without a report array");
+    if (n_out) *n_out = 0;
+    PlanParams keep = c->pp;
+    int rc = tune_impl(c, m_max, reps, report, cap, n_out);
+    if (rc) {
+        c->pp = keep;   // a failed run leaves the table as it was
+        drop_graphs(c);
+    }
+    return rc;
+}
+
+int hg_get_tuning(hg_ctx *c, int16_t *table)
+{
+    if (!c || !table) return HG_EINVAL;
+    for (int k = 0; k < kTuneBuckets; ++k) table[k] = c->pp.tuned[k];
+    return HG_OK;
+}
+
+int hg_set_tuning(hg_ctx *c, const int16_t *table)
+{
+    if (!c || !table) return HG_EINVAL;
+    for (int k = 0; k < kTuneBuckets; ++k) {
+        const int v = table[k];
+        const bool ok = v == -1 || (c->bv.nc > 0 ? batch_code_ok(v) : (v >= 0 && v < kPlanCandidates));
+        if (!ok) return fail(c, HG_EINVAL, "tuning table value out of range for this context");
+    }
+    for (int k = 0; k < kTuneBuckets; ++k) c->pp.tuned[k] = table[k];
+    drop_graphs(c);
     return HG_OK;
 }
 

@@ -567,6 +567,7 @@ PlanParams plan_params(bool mixed, int64_t npad, int num_sms, int64_t pcap, int 
     q.b_force = b_force;
     q.c_tile = mixed ? 2 : 1;
     q.c_item = mixed ? 24 : 2;
+    for (int k = 0; k < kTuneBuckets; ++k) q.tuned[k] = -1;
     return q;
 }
 

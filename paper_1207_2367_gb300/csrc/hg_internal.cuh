@@ -71,6 +71,8 @@ struct Plan {
     int64_t n_itiles, tiles_per_split, n_items;
 };
 
+constexpr int kTuneBuckets = HG_TUNE_BUCKETS;   // block sizes 2^k <= m < 2^(k+1)
+
 // Inputs of the planner that do not change between block steps.
 struct PlanParams {
     int64_t ntiles;      // j-tiles of npad records
@@ -78,7 +80,17 @@ struct PlanParams {
     int i_per_thread, tj, grid;
     int tpi_force, b_force;
     int c_tile, c_item;  // per-tile and per-item overhead, in j-iterations of one thread
+    // Measured choices per block-size bucket (-1: cost model).  One system: a
+    // candidate index; clusters: a batch code (see batch_knobs).
+    int16_t tuned[kTuneBuckets];
 };
+
+__host__ __device__ inline int tune_bucket(int64_t m)
+{
+    int k = 0;
+    while (k < kTuneBuckets - 1 && (m >> (k + 1)) > 0) ++k;
+    return k;
+}
 
 // Candidate c in [0, kPlanCandidates): threads per i = 2^(c / 32), tiles per
 // split from kTps[c % 32].
@@ -118,10 +130,13 @@ __host__ __device__ inline int64_t plan_candidate(int64_t m, const PlanParams &q
     return waves * (tps * (q.tj / tpi + q.c_tile) + q.c_item);
 }
 
-// The cheapest admissible candidate (ties: lowest candidate index).
+// The tuned candidate of m's bucket if there is one and it is admissible, else
+// the cheapest admissible candidate of the cost model (ties: lowest index).
 __host__ __device__ inline Plan make_plan(int64_t m, const PlanParams &q)
 {
     Plan best{}, p{};
+    const int tc = q.tuned[tune_bucket(m)];
+    if (tc >= 0 && tc < kPlanCandidates && plan_candidate(m, q, tc, p) >= 0) return p;
     int64_t best_cost = -1;
     for (int c = 0; c < kPlanCandidates; ++c) {
         const int64_t cost = plan_candidate(m, q, c, p);
@@ -155,6 +170,24 @@ struct BatchView {
 };
 
 constexpr int kBatchTpsMax = 64;   // tiles per j-chunk considered by the batch planner
+
+// Knobs of the batch planner for a block of m: the j-split leaves at least
+// 2^w_log work items per resident CTA; threads per i-particle are scaled by
+// 2^tpi_shift.  Code w + 8 (s + 1); -1 (untuned): w = 1, s = 0.
+struct BatchKnobs {
+    int w_log, tpi_shift;
+};
+constexpr int kBatchWMax = 6;
+__host__ __device__ inline bool batch_code_ok(int v)
+{
+    return v >= 0 && (v & 7) <= kBatchWMax && (v >> 3) <= 2;
+}
+__host__ __device__ inline BatchKnobs batch_knobs(int64_t m, const PlanParams &q)
+{
+    const int v = q.tuned[tune_bucket(m)];
+    if (!batch_code_ok(v)) return BatchKnobs{1, 0};
+    return BatchKnobs{v & 7, (v >> 3) - 1};
+}
 
 struct EvalArgs {
     Records rec;

@@ -62,6 +62,11 @@ __device__ void plan_on_device(int64_t m, const PlanParams &q, DevScalars *sc)
     int64_t best = -1;
     int bc = 0x7fffffff;
     Plan p;
+    const int tc = q.tuned[tune_bucket(m)];
+    if (tc >= 0 && tc < kPlanCandidates && plan_candidate(m, q, tc, p) >= 0) {   // measured choice
+        if (lane == 0) *reinterpret_cast<Plan *>(sc->plan) = p;
+        return;
+    }
     for (int c = lane; c < kPlanCandidates; c += 32) {
         const int64_t cost = plan_candidate(m, q, c, p);
         if (cost >= 0 && (best < 0 || cost < best)) {
@@ -760,15 +765,29 @@ __device__ void block_exscan_i64(int64_t v, int64_t *sh, int64_t &excl, int64_t 
     __syncthreads();
 }
 
+// Threads per i-particle of a cluster with mc active particles: the largest
+// power of two that still fills one CTA (ipt particles per thread), times 2^shift.
+__device__ __forceinline__ int batch_tpi(int64_t mc, int ipt, int shift)
+{
+    int tpi = 1;
+    const int64_t want = (int64_t)kEvalThreads * ipt / mc;
+    while (tpi * 2 <= want && tpi < kMaxTPI) tpi *= 2;
+    if (shift > 0 && tpi < kMaxTPI) tpi *= 2;
+    if (shift < 0 && tpi > 1) tpi /= 2;
+    return tpi;
+}
+
 __global__ void __launch_bounds__(kPlanThreads) k_batch_plan(const int32_t *idx, const int64_t *m_dev, int64_t m_host,
-                                                             BatchView bv, int tj, int ipt, int grid, int64_t pcap,
-                                                             DevScalars *count)
+                                                             BatchView bv, PlanParams q, DevScalars *count)
 {
     __shared__ int64_t sh[33];
     __shared__ int64_t s_tps;
     const int64_t m = m_dev ? *m_dev : m_host;
     if (m <= 0) return;
     const int nc = bv.nc;
+    const int tj = q.tj, ipt = q.i_per_thread, grid = q.grid;
+    const int64_t pcap = q.pcap;
+    const BatchKnobs kn = batch_knobs(m, q);
     for (int c = threadIdx.x; c <= nc; c += blockDim.x) {
         if (c == nc) {
             bv.a_off[nc] = m;
@@ -791,9 +810,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_batch_plan(const int32_t *idx,
     for (int c = c0; c < c1; ++c) {
         const int64_t mc = bv.a_off[c + 1] - bv.a_off[c];
         if (mc == 0) continue;
-        int tpi = 1;
-        const int64_t want = (int64_t)kEvalThreads * ipt / mc;
-        while (tpi * 2 <= want && tpi < kMaxTPI) tpi *= 2;
+        const int tpi = batch_tpi(mc, ipt, kn.tpi_shift);
         const int64_t ti = kEvalThreads / tpi * ipt;
         const int64_t nit = (mc + ti - 1) / ti;
         const int64_t ntc = (bv.rec_off[c + 1] - bv.rec_off[c]) / tj;
@@ -813,7 +830,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_batch_plan(const int32_t *idx,
     if (threadIdx.x == 0) {
         int pick = -1;
         for (int k = kTpsCand - 1; k >= 0 && pick < 0; --k)
-            if (parts[k] <= pcap && items[k] >= 2 * (int64_t)grid) pick = k;
+            if (parts[k] <= pcap && items[k] >= ((int64_t)grid << kn.w_log)) pick = k;
         for (int k = 0; k < kTpsCand && pick < 0; ++k)
             if (parts[k] <= pcap) pick = k;
         if (pick < 0) pick = kTpsCand - 1;
@@ -825,11 +842,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_batch_plan(const int32_t *idx,
     int64_t my_items = 0, my_parts = 0;
     for (int c = c0; c < c1; ++c) {
         const int64_t mc = bv.a_off[c + 1] - bv.a_off[c];
-        int tpi = 1;
-        if (mc > 0) {
-            const int64_t want = (int64_t)kEvalThreads * ipt / mc;
-            while (tpi * 2 <= want && tpi < kMaxTPI) tpi *= 2;
-        }
+        const int tpi = mc > 0 ? batch_tpi(mc, ipt, kn.tpi_shift) : 1;
         const int64_t ti = kEvalThreads / tpi * ipt;
         const int64_t nit = (mc + ti - 1) / ti;
         const int64_t ntc = (bv.rec_off[c + 1] - bv.rec_off[c]) / tj;
@@ -965,10 +978,10 @@ cudaError_t launch_pad_records(bool mixed, const Records &rec, int64_t npad, cud
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_plan(const int32_t *idx, const int64_t *m_dev, int64_t m_host, const BatchView &bv, int tj,
-                              int ipt, int grid, int64_t pcap, DevScalars *count, cudaStream_t s)
+cudaError_t launch_batch_plan(const int32_t *idx, const int64_t *m_dev, int64_t m_host, const BatchView &bv,
+                              const PlanParams &q, DevScalars *count, cudaStream_t s)
 {
-    k_batch_plan<<<1, kPlanThreads, 0, s>>>(idx, m_dev, m_host, bv, tj, ipt, grid, pcap, count);
+    k_batch_plan<<<1, kPlanThreads, 0, s>>>(idx, m_dev, m_host, bv, q, count);
     return cudaGetLastError();
 }
 

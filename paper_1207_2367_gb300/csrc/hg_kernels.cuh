@@ -31,10 +31,11 @@ cudaError_t launch_predict_clusters(bool mixed, const State &st, const Records &
                                     const double *t_dev, const int64_t *m_dev, cudaStream_t s);
 // Padding in every record slot (cluster contexts, before the first prediction).
 cudaError_t launch_pad_records(bool mixed, const Records &rec, int64_t npad, cudaStream_t s);
-// Work list of one evaluation over clusters (sizes on the device or host);
-// count != nullptr adds the step's pair evaluations to count->interactions.
-cudaError_t launch_batch_plan(const int32_t *idx, const int64_t *m_dev, int64_t m_host, const BatchView &bv, int tj,
-                              int ipt, int grid, int64_t pcap, DevScalars *count, cudaStream_t s);
+// Work list of one evaluation over clusters (sizes on the device or host), with
+// the knobs of q.tuned for the block's size; count != nullptr adds the step's
+// pair evaluations to count->interactions.
+cudaError_t launch_batch_plan(const int32_t *idx, const int64_t *m_dev, int64_t m_host, const BatchView &bv,
+                              const PlanParams &q, DevScalars *count, cudaStream_t s);
 cudaError_t launch_start(const State &st, int64_t n, const double *ra, const double *rj, const double *rs,
                          const StepParams &sp, cudaStream_t s);
 cudaError_t launch_correct(const State &st, const int32_t *idx, const int64_t *m_dev, int64_t m_host, int64_t n_max,

@@ -1,0 +1,37 @@
+// Host-side check of the evaluation planner (hg_internal.cuh): prints, for
+// each query line "m tuned_value" read from stdin, the bucket and the plan
+// chosen with that value stored in m's bucket ("-" for the cost model alone).
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "hg_internal.cuh"
+
+int main(int argc, char **argv)
+{
+    // Planner inputs of a mixed context with n = 65536 on 152 SMs.
+    const long long npad = argc > 1 ? atoll(argv[1]) : 65536;
+    hg::PlanParams q{};
+    q.tj = hg::kTJMixed;
+    q.i_per_thread = hg::kIMixed;
+    q.ntiles = npad / q.tj;
+    q.pcap = 4 * npad > (1 << 20) ? 4 * npad : (1 << 20);
+    q.grid = 4 * 152;
+    q.tpi_force = 0;
+    q.b_force = 0;
+    q.c_tile = 2;
+    q.c_item = 24;
+    long long m;
+    int v;
+    while (scanf("%lld %d", &m, &v) == 2) {
+        for (int k = 0; k < hg::kTuneBuckets; ++k) q.tuned[k] = -1;
+        const int b = hg::tune_bucket(m);
+        const hg::Plan model = hg::make_plan(m, q);
+        q.tuned[b] = (int16_t)v;
+        const hg::Plan p = hg::make_plan(m, q);
+        const hg::BatchKnobs kn = hg::batch_knobs(m, q);
+        printf("%d %d %lld %d %lld %d %d %d\n", b, model.tpi, (long long)model.tiles_per_split, p.tpi,
+               (long long)p.tiles_per_split, p.b, kn.w_log, kn.tpi_shift);
+    }
+    return 0;
+}
