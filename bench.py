@@ -46,6 +46,10 @@ NUM_SMS = 152
 EVAL_TRAFFIC = {(65536, "equal", "mixed"): 3.47e6}
 
 
+def parse_defaults():
+    return {"n": 65536, "imf": "equal", "seed": 2}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -66,6 +70,11 @@ def parse():
     ap.add_argument("--batch", action="store_true",
                     help="independent-clusters workload: batched context vs one context per cluster")
     ap.add_argument("--clusters", type=int, default=512)
+    ap.add_argument("--mode", choices=["interval", "batch", "block-sizes", "accuracy", "large"], default="interval",
+                    help="interval: the default line; batch: 512 clusters; block-sizes: evaluation time per "
+                         "block-size bucket, FP64 and mixed, N = 65536 to t = 1/8; accuracy: N = 2^20 Salpeter, "
+                         "mixed vs FP64 per block step and |dE/E| of both; large: N = 2^23 Salpeter, 32 block "
+                         "steps including the start-up evaluation")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the cost model's launch plans (no hg_tune before the warm-up)")
     return ap.parse_args()
@@ -481,10 +490,219 @@ def run_batch(a):
     }), flush=True)
 
 
+# ----------------------------------------------------------------------------
+# Further configurations (one JSON line each; not the driver's default line).
+# ----------------------------------------------------------------------------
+def _device_state(hg, ctx, n):
+    import torch
+    st = hg.new_state(n, like="cuda")
+    t = hg.hg_get_state(ctx, st)
+    return st, t
+
+
+def _rel_stats(got, ref):
+    """Normwise and per-particle relative errors of an [m][3] result."""
+    g, r = np.asarray(got).reshape(-1, 3), np.asarray(ref).reshape(-1, 3)
+    den = np.linalg.norm(r, axis=1)
+    per = np.linalg.norm(g - r, axis=1) / np.where(den > 0, den, 1.0)
+    return {"normwise": float(np.linalg.norm(g - r) / np.linalg.norm(r)), "max": float(per.max()),
+            "median": float(np.median(per)), "p99": float(np.quantile(per, 0.99))}
+
+
+def run_block_sizes(a):
+    """Evaluation time of every block size that occurs from t = 0 to 1/8 on the
+    N = 65536 Plummer sphere (eps 1e-4), FP64 and mixed, grouped in power-of-two
+    buckets of m; CUDA events around each graph-replayed evaluation."""
+    import torch
+    from paper_1207_2367_gb300 import binding as hg
+    from paper_1207_2367_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    hg.load()
+    stream = torch.cuda.Stream()
+    mhz, kind = sm_max_mhz()
+    p = inputs.plummer(a.n, a.seed, imf=a.imf)
+    out = {"metric": "evaluation time per block-size bucket", "unit": "us",
+           "config": {"workload": f"Plummer N={a.n}, {a.imf} masses (seed {a.seed}), eps={a.eps:g}, eta=0.45, "
+                                  "dt_max=1/16, t = 0 -> 1/8, every block step"}}
+    for prec, name in ((hg.HG_FP64, "fp64"), (hg.HG_MIXED, "mixed")):
+        ctx = make_ctx(hg, p, a, prec, stream, 0)
+        tuning = tune(hg, ctx, a)
+        buckets = {}
+        hg.hg_get_profile(ctx, reset=True)
+        while True:
+            hg.hg_step(ctx, 1)
+            st = hg.hg_get_stats(ctx)
+            if st["t_sys"] > 0.125:
+                break
+            pr = hg.hg_get_profile(ctx, reset=True)["ms"]
+            m = st["last_m"]
+            b = buckets.setdefault(m.bit_length() - 1, {"steps": 0, "m_sum": 0, "eval_ms": 0.0, "step_ms": 0.0})
+            b["steps"] += 1
+            b["m_sum"] += m
+            b["eval_ms"] += pr["evaluate"] + pr["reduce"]
+            b["step_ms"] += sum(pr.values())
+        hg.hg_free(ctx)
+        peak = fp64_peak_tflops(mhz) if prec == hg.HG_FP64 else fp32_peak_tflops(mhz)
+        rows = []
+        for k in sorted(buckets):
+            b = buckets[k]
+            inter = b["m_sum"] * a.n
+            rate = inter / (b["eval_ms"] / 1e3)
+            rows.append({"bucket": f"[{1 << k}, {(2 << k) - 1}]", "steps": b["steps"],
+                         "mean_m": b["m_sum"] / b["steps"], "eval_us": 1e3 * b["eval_ms"] / b["steps"],
+                         "step_us": 1e3 * b["step_ms"] / b["steps"], "interactions_per_s": rate,
+                         "gflops_77": rate * 77 / 1e9, "gflops_paper_97": rate * PAPER_FLOPS / 1e9,
+                         "frac_of_peak": rate * 77 / 1e12 / peak})
+        out[name] = {"buckets": rows, "peak_tflops": peak, "tuning": tuning}
+    print(json.dumps(out), flush=True)
+
+
+def run_accuracy(a):
+    """N = 2^20 Salpeter (seed 3), eps 1e-4: 64 block steps of the mixed path;
+    at each, the mixed evaluation of the block against the FP64 kernel on the same
+    state (FP64 context given the mixed context's state, both predicting to the
+    block time); then 64 block steps of the FP64 path from its own start-up, and
+    |dE/E| of both with FP64 pair energies at their last block times."""
+    import torch
+    from paper_1207_2367_gb300 import binding as hg
+    from paper_1207_2367_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    hg.load()
+    stream = torch.cuda.Stream()
+    n, steps = a.n, (a.block_steps or 64)
+    p = inputs.plummer(n, a.seed, imf=a.imf)
+
+    def opts(prec, start_mode=0):
+        return hg.hg_default_opts(precision=prec, energy_precision=hg.HG_FP64, dt_max=1.0 / 16, stream=stream,
+                                  start_mode=start_mode)
+
+    mix = hg.hg_init(p.mass, p.pos, p.vel, a.eps, 0.45, opts(hg.HG_MIXED))
+    ref = hg.hg_init(p.mass, p.pos, p.vel, a.eps, 0.45, opts(hg.HG_FP64, start_mode=1))
+    E0 = sum(hg.hg_energy(mix))
+    per_step, worst = [], {"acc": 0.0, "jerk": 0.0, "snap": 0.0}
+    idx = np.empty(n, dtype=np.int32)
+    for _ in range(steps):
+        st, t_sys = _device_state(hg, mix, n)
+        hg.hg_set_state(ref, st, t_sys)
+        t, m = hg.hg_next_block(mix, idx)
+        lst = np.ascontiguousarray(idx[:m])
+        got = [np.empty((m, 3)) for _ in range(3)]
+        want = [np.empty((m, 3)) for _ in range(3)]
+        hg.hg_predict(mix, t)
+        hg.hg_evaluate(mix, None, m, *got)
+        hg.hg_predict(ref, t)
+        hg.hg_evaluate(ref, lst, m, *want)
+        hg.hg_correct(mix, None, m)
+        row = {"t": t, "m": m}
+        for name, g, w in zip(("acc", "jerk", "snap"), got, want):
+            row[name] = _rel_stats(g, w)
+            worst[name] = max(worst[name], row[name]["normwise"])
+        per_step.append(row)
+        del st
+    hg.hg_free(ref)
+    t_mix = hg.hg_get_stats(mix)["t_sys"]
+    dE_mix = abs((sum(hg.hg_energy(mix)) - E0) / E0)
+    hg.hg_free(mix)
+
+    f64 = hg.hg_init(p.mass, p.pos, p.vel, a.eps, 0.45, opts(hg.HG_FP64))
+    torch.cuda.synchronize()
+    hg.hg_step(f64, steps)
+    t_f64 = hg.hg_get_stats(f64)["t_sys"]
+    dE_f64 = abs((sum(hg.hg_energy(f64)) - E0) / E0)
+    hg.hg_free(f64)
+    ms = [r["m"] for r in per_step]
+    print(json.dumps({
+        "metric": "mixed vs FP64 relative error per block step; |dE/E| of both paths",
+        "config": {"workload": f"Plummer N={n}, {a.imf} masses (seed {a.seed}), eps={a.eps:g}, eta=0.45, "
+                               f"dt_max=1/16, {steps} block steps after the start-up evaluation"},
+        "tolerance": {"acc": 1e-6, "jerk": 1e-5, "snap": 1e-4},
+        "max_normwise": worst,
+        "max_per_particle": {k: max(r[k]["max"] for r in per_step) for k in ("acc", "jerk", "snap")},
+        "median_per_particle": {k: float(np.median([r[k]["median"] for r in per_step]))
+                                for k in ("acc", "jerk", "snap")},
+        "block_sizes": {"min": min(ms), "max": max(ms), "mean": float(np.mean(ms))},
+        "dE_over_E": {"mixed": dE_mix, "fp64": dE_f64, "t_mixed": t_mix, "t_fp64": t_f64},
+        "steps": per_step,
+    }), flush=True)
+
+
+def run_large(a):
+    """N = 2^23 Salpeter (seed 5), eps 1e-4, mixed: the start-up evaluation
+    (all N active) plus 31 block steps, timed; then a seeded (seed 6) subset of
+    4096 particles evaluated by the mixed and the FP64 kernels on the same state."""
+    import torch
+    from paper_1207_2367_gb300 import binding as hg
+    from paper_1207_2367_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    hg.load()
+    stream = torch.cuda.Stream()
+    n, steps = a.n, (a.block_steps or 31)
+    p = inputs.plummer(n, a.seed, imf=a.imf)
+    mhz, kind = sm_max_mhz()
+    o = hg.hg_default_opts(precision=hg.HG_MIXED, energy_precision=hg.HG_MIXED, dt_max=1.0 / 16, stream=stream,
+                           profile=1)
+    torch.cuda.synchronize()
+    ev0, ev1, ev2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    ev0.record(stream)
+    ctx = hg.hg_init(p.mass, p.pos, p.vel, a.eps, 0.45, o)
+    ev1.record(stream)
+    hg.hg_step(ctx, steps)
+    ev2.record(stream)
+    ev2.synchronize()
+    init_ms, steps_ms = ev0.elapsed_time(ev1), ev1.elapsed_time(ev2)
+    st = hg.hg_get_stats(ctx)
+    prof = hg.hg_get_profile(ctx)
+    inter = n * n + st["interactions"]
+    # accuracy on a seeded subset, same state for both kernels
+    rng = np.random.default_rng(6)
+    lst = np.sort(rng.choice(n, 4096, replace=False)).astype(np.int32)
+    dst, t_sys = _device_state(hg, ctx, n)
+    ref = hg.hg_init(p.mass, p.pos, p.vel, a.eps, 0.45,
+                     hg.hg_default_opts(precision=hg.HG_FP64, dt_max=1.0 / 16, stream=stream, start_mode=1))
+    hg.hg_set_state(ref, dst, t_sys)
+    del dst
+    t = t_sys + 2.0 ** -20
+    got = [np.empty((4096, 3)) for _ in range(3)]
+    want = [np.empty((4096, 3)) for _ in range(3)]
+    hg.hg_predict(ctx, t)
+    hg.hg_evaluate(ctx, lst, 4096, *got)
+    hg.hg_predict(ref, t)
+    hg.hg_evaluate(ref, lst, 4096, *want)
+    hg.hg_free(ref)
+    hg.hg_free(ctx)
+    total_s = (init_ms + steps_ms) / 1e3
+    rate = inter / total_s
+    print(json.dumps({
+        "metric": "acc/jerk/snap interactions/s and % FP32 peak (N = 2^23)", "unit": "interactions/s",
+        "value": rate, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"Plummer N={n}, {a.imf} masses (seed {a.seed}), eps={a.eps:g}, eta=0.45, "
+                               f"start-up evaluation + {steps} block steps, mixed precision"},
+        "startup": {"ms": init_ms, "interactions": n * n, "rate": n * n / (init_ms / 1e3),
+                    "note": "hg_init: upload, validation, all-active evaluation, first steps"},
+        "block_steps": {"ms": steps_ms, "interactions": st["interactions"], "steps": st["block_steps"],
+                        "sections_ms": prof["ms"]},
+        "frac_of_fp32_peak": rate * FLOPS_F32 / 1e12 / fp32_peak_tflops(mhz),
+        "subset_vs_fp64": {name: _rel_stats(g, w) for name, g, w in zip(("acc", "jerk", "snap"), got, want)},
+        "subset": "4096 particles (numpy default_rng(6) choice), predicted 2^-20 past the last block time",
+    }), flush=True)
+
+
 def main():
     a = parse()
-    if a.batch:
+    if a.batch or a.mode == "batch":
         run_batch(a)
+        return
+    modes = {"block-sizes": run_block_sizes, "accuracy": run_accuracy, "large": run_large}
+    if a.mode in modes:
+        defaults = {"accuracy": dict(n=1 << 20, imf="salpeter", seed=3),
+                    "large": dict(n=1 << 23, imf="salpeter", seed=5)}.get(a.mode, {})
+        for k, v in defaults.items():
+            if getattr(a, k) == parse_defaults()[k]:
+                setattr(a, k, v)
+        modes[a.mode](a)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
