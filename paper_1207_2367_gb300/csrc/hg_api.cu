@@ -123,6 +123,7 @@ StepParams step_params(const hg_ctx *c)
     // FP32 pair arithmetic resolves accelerations to ~1e-7 relative; a change
     // below 3e-6 |a| carries no usable higher-derivative information.
     p.noise_rel = c->mixed ? 3e-6 : 0.0;
+    p.log2_eta = (float)log2(c->eta);
     return p;
 }
 

@@ -53,21 +53,24 @@ __device__ __forceinline__ long long block_min_ll(long long v, long long *sh)
     return sh[0];
 }
 
-// The evaluation plan for block size m, by one warp: lane l scores candidates
-// l, l + 32, ...; the lowest cost wins, ties to the lowest candidate index
-// (the same choice make_plan makes on the host).
-__device__ void plan_on_device(int64_t m, const PlanParams &q, DevScalars *sc)
+// The evaluation plan for block size m, by every thread of one CTA (at least
+// kPlanCandidates threads would score one candidate each; fewer loop): the
+// lowest cost wins, ties to the lowest candidate index (make_plan's choice on
+// the host).  A tuned candidate of m's bucket that is admissible wins outright.
+__device__ void plan_on_block(int64_t m, const PlanParams &q, DevScalars *sc)
 {
-    const int lane = threadIdx.x & 31;
-    int64_t best = -1;
-    int bc = 0x7fffffff;
+    __shared__ int64_t s_cost[32];
+    __shared__ int s_cand[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
     Plan p;
     const int tc = q.tuned[tune_bucket(m)];
     if (tc >= 0 && tc < kPlanCandidates && plan_candidate(m, q, tc, p) >= 0) {   // measured choice
-        if (lane == 0) *reinterpret_cast<Plan *>(sc->plan) = p;
+        if (threadIdx.x == 0) *reinterpret_cast<Plan *>(sc->plan) = p;
         return;
     }
-    for (int c = lane; c < kPlanCandidates; c += 32) {
+    int64_t best = -1;
+    int bc = 0x7fffffff;
+    for (int c = threadIdx.x; c < kPlanCandidates; c += blockDim.x) {
         const int64_t cost = plan_candidate(m, q, c, p);
         if (cost >= 0 && (best < 0 || cost < best)) {
             best = cost;
@@ -83,9 +86,21 @@ __device__ void plan_on_device(int64_t m, const PlanParams &q, DevScalars *sc)
         }
     }
     if (lane == 0) {
+        s_cost[w] = best;
+        s_cand[w] = bc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < nw; ++k) {
+            const int64_t ob = s_cost[k];
+            const int oc = s_cand[k];
+            if (ob >= 0 && (best < 0 || ob < best || (ob == best && oc < bc))) {
+                best = ob;
+                bc = oc;
+            }
+        }
         plan_candidate(m, q, best >= 0 ? bc : 0, p);
-        Plan *dst = reinterpret_cast<Plan *>(sc->plan);
-        *dst = p;
+        *reinterpret_cast<Plan *>(sc->plan) = p;
     }
 }
 
@@ -190,7 +205,7 @@ __global__ void __launch_bounds__(kNBThreads) k_nb_count(const double *tend, int
             sc->done = 1;
         }
     }
-    if (take && threadIdx.x < 32) plan_on_device(tot, pq, sc);
+    if (take) plan_on_block(tot, pq, sc);   // uniform branch: every thread of the CTA
 }
 
 __global__ void __launch_bounds__(kNBThreads) k_nb_scatter(const double *tend, int64_t n, int64_t chunk,
@@ -463,15 +478,52 @@ __global__ void k_start(State st, int64_t n, const double *ra, const double *rj,
 // p = 6 criterion and the new block step, for the m particles of the block.
 // ------------------------------------------------------------------------
 
+// Exact powers of two from integer exponents (no FP64 instruction on the
+// normal range; GB300 issues a warp-wide FP64 instruction in ~64 cycles, so the
+// corrector's latency is its count of dependent FP64 instructions).
+__device__ __forceinline__ double pow2i(int e)
+{
+    if (e > 1023) return INFINITY;
+    if (e < -1022) return ldexp(1.0, e);
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+// Exponent k of h = 2^k (normal, positive); false if h is not such a power of two.
+__device__ __forceinline__ bool pow2_exponent(double h, int &k)
+{
+    const long long b = __double_as_longlong(h);
+    const int be = (int)((b >> 52) & 0x7ff);
+    if (b <= 0 || be == 0 || be == 0x7ff || (b & 0xfffffffffffffLL) != 0) return false;
+    k = be - 1023;
+    return true;
+}
+
 // Component k of particle i over its step h: corrected v and r (stored, with
 // the new a, jerk, snap and crackle), and crackle, pop and a^(5) from the
 // degree-5 interpolant through a, jerk, snap at both ends of the step.
-__device__ __forceinline__ void correct_component(const State &st, int64_t i, int k, double h, double a1, double j1,
-                                                  double s1, double &c3, double &c4, double &c5, double &Ak)
+// h = 2^e: h/2, h^2/10 = 2^(2e) fl(1/10), h^3/120 = 2^(3e) fl(1/120) and the
+// reciprocal powers are exact scalings, equal to the divisions they replace.
+__device__ __forceinline__ void correct_component(const State &st, int64_t i, int k, double h, int e, bool pow2,
+                                                  double a1, double j1, double s1, double &c3, double &c4, double &c5,
+                                                  double &Ak)
 {
-    const double hh = h / 2.0, h2 = h * h / 10.0, h3 = h * h * h / 120.0;
-    // h is a power of two: its reciprocal powers are exact.
-    const double ih = 1.0 / h, ih3 = ih * ih * ih, ih4 = ih3 * ih, ih5 = ih4 * ih;
+    double hh, h2, h3, ih3, ih4, ih5;
+    if (pow2) {
+        hh = pow2i(e - 1);
+        h2 = pow2i(2 * e) * 0.1;
+        h3 = pow2i(3 * e) * (1.0 / 120.0);
+        ih3 = pow2i(-3 * e);
+        ih4 = pow2i(-4 * e);
+        ih5 = pow2i(-5 * e);
+    } else {
+        hh = h / 2.0;
+        h2 = h * h / 10.0;
+        h3 = h * h * h / 120.0;
+        const double ih = 1.0 / h;
+        ih3 = ih * ih * ih;
+        ih4 = ih3 * ih;
+        ih5 = ih4 * ih;
+    }
     const int64_t q = 3 * i + k;
     const double x0 = st.x[q], v0 = st.v[q], a0 = st.a[q], j0 = st.j[q], s0 = st.s[q];
     const double v1 = v0 + hh * (a1 + a0) - h2 * (j1 - j0) + h3 * (s1 + s0);
@@ -491,17 +543,120 @@ __device__ __forceinline__ void correct_component(const State &st, int64_t i, in
     st.c[q] = c3;
 }
 
+// ---- FP32 estimate of floor(log2 crit) for the p = 6 criterion -------------
+// Logarithms are carried as e + r: an exact integer e and a small float r, so
+// that exponents up to +-2046 keep ~1e-7 absolute precision.  Every step below
+// (mantissa truncated to 24 bits, lg2/ex2 approximations) errs by < 1e-6 in
+// log2 units; an estimate within kLogGuard of an integer is decided by the FP64
+// criterion instead, so the step chosen is always the FP64 criterion's.
+struct Log2 {
+    int e;
+    float r;
+};
+constexpr float kLogGuard = 1.0e-4f;
+
+__device__ __forceinline__ bool log2_of(double q, Log2 &o)
+{
+    const long long b = __double_as_longlong(q);
+    const int be = (int)((b >> 52) & 0x7ff);
+    if (b <= 0 || be == 0 || be == 0x7ff) return false;   // zero, negative, subnormal, inf, nan
+    o.e = be - 1023;
+    o.r = __log2f(__int_as_float(0x3f800000 | (int)((b >> 29) & 0x7fffff)));   // mantissa in [1, 2)
+    return true;
+}
+__device__ __forceinline__ Log2 l2_add(Log2 a, Log2 b) { return Log2{a.e + b.e, a.r + b.r}; }
+// x / d for d = 2, 3 or 6: e = d k + j (floor division), x / d = k + (j + r) / d.
+__device__ __forceinline__ Log2 l2_div(Log2 a, int d)
+{
+    int k = a.e / d, j = a.e - k * d;
+    if (j < 0) {
+        j += d;
+        k -= 1;
+    }
+    return Log2{k, ((float)j + a.r) / (float)d};
+}
+// log2(2^a + 2^b)
+__device__ __forceinline__ Log2 l2_sum(Log2 a, Log2 b)
+{
+    float d = (float)(a.e - b.e) + (a.r - b.r);
+    if (d < 0.0f) {
+        const Log2 t = a;
+        a = b;
+        b = t;
+        d = -d;
+    }
+    if (d > 60.0f) return a;
+    return Log2{a.e, a.r + __log2f(1.0f + exp2f(-d))};
+}
+
+// floor(log2(eta (A1 / A4)^(1/3))) with A1 = sqrt(n0 n2 + n1^2), A4 = sqrt(n3 n5 + n4^2),
+// n_s = |d_s|, from the squared norms q_s; false when undecided (a q_s that is
+// zero or not normal, or the estimate within kLogGuard of an integer).
+__device__ __forceinline__ bool criterion6_floor_log2(const double *qn, float log2_eta, int &F)
+{
+    Log2 l[6];
+#pragma unroll
+    for (int s = 0; s < 6; ++s)
+        if (!log2_of(qn[s], l[s])) return false;
+    // log2 A^2 terms: log2(n0 n2) = (L0 + L2) / 2, log2(n1^2) = L1 (L = log2 q).
+    const Log2 A1sq = l2_sum(l2_div(l2_add(l[0], l[2]), 2), l[1]);
+    const Log2 A4sq = l2_sum(l2_div(l2_add(l[3], l[5]), 2), l[4]);
+    // log2 crit = log2 eta + (log2 A1^2 - log2 A4^2) / 6
+    const Log2 x = l2_div(Log2{A1sq.e - A4sq.e, A1sq.r - A4sq.r}, 6);
+    const float y = log2_eta + x.r;
+    const float fy = floorf(y);
+    const float frac = y - fy;
+    if (frac < kLogGuard || frac > 1.0f - kLogGuard) return false;
+    F = x.e + (int)fy;
+    return true;
+}
+
+// t1 (>= 0, dyadic) is an integer multiple of 2^p: the lowest set bit of its
+// significand weighs at least 2^p.  Subnormal t1: fmod.
+__device__ __forceinline__ bool multiple_of_pow2(double t1, int p)
+{
+    if (t1 == 0.0) return true;
+    const long long b = __double_as_longlong(t1);
+    const int be = (int)((b >> 52) & 0x7ff);
+    if (be == 0 || b < 0) return fmod(t1, pow2i(p)) == 0.0;
+    const long long mant = (b & 0xfffffffffffffLL) | (1LL << 52);
+    return (be - 1023 - 52) + (__ffsll(mant) - 1) >= p;
+}
+
+__device__ __forceinline__ double sq3(const double *p) { return p[0] * p[0] + p[1] * p[1] + p[2] * p[2]; }
+
 // New time and p = 6 step of particle i from d = a^(0..5) at the step's end.
 // A: the acceleration change left after a0 + j0 h + s0 h^2/2.  Below the noise
-// floor of the evaluation (sp.noise_rel |a1|) the interpolated derivatives are
-// noise and the criterion is not allowed to shrink the step.
-__device__ __forceinline__ void finish_step(const State &st, int64_t i, double h, const double (*d)[3],
-                                            const double *A, const StepParams &sp)
+// floor of the evaluation (sp.noise_rel |a1|, compared as squares) the
+// interpolated derivatives are noise and the criterion may not shrink the step.
+__device__ __forceinline__ void finish_step(const State &st, int64_t i, double h, int e, bool pow2,
+                                            const double (*d)[3], const double *A, const StepParams &sp)
 {
     const double t1 = st.t[i] + h;
-    double crit = criterion(sp.eta, 6, d);
-    if (sp.noise_rel > 0.0 && norm3(A) < sp.noise_rel * norm3(d[0])) crit = INFINITY;
-    const double dt1 = block_dt(crit, h, t1, sp.dt_min, sp.dt_max);
+    const bool noisy = sp.noise_rel > 0.0 && sq3(A) < (sp.noise_rel * sp.noise_rel) * sq3(d[0]);
+    double dt1;
+    int F, kmin, kmax;
+    double qn[6];
+#pragma unroll
+    for (int s = 0; s < 6; ++s) qn[s] = sq3(d[s]);
+    if (pow2 && pow2_exponent(sp.dt_min, kmin) && pow2_exponent(sp.dt_max, kmax) &&
+        (noisy || criterion6_floor_log2(qn, sp.log2_eta, F))) {
+        // The power-of-two rule (block_dt) on exponents: shrink to max(F, k_min)
+        // when crit < h, double when crit >= 2h, 2h <= dt_max and t1 is a
+        // multiple of 2h; clamp to [dt_min, dt_max].
+        int kn = e;
+        if (!noisy && F < e) {
+            kn = F > kmin ? F : kmin;
+        } else if ((noisy || F >= e + 1) && e + 1 <= kmax && multiple_of_pow2(t1, e + 1)) {
+            kn = e + 1;
+        }
+        kn = kn < kmin ? kmin : (kn > kmax ? kmax : kn);
+        dt1 = pow2i(kn);
+    } else {
+        double crit = criterion(sp.eta, 6, d);
+        if (noisy) crit = INFINITY;
+        dt1 = block_dt(crit, h, t1, sp.dt_min, sp.dt_max);
+    }
     st.t[i] = t1;
     st.dt[i] = dt1;
     st.tend[i] = t1 + dt1;
@@ -514,11 +669,13 @@ __global__ void k_correct(State st, const int32_t *idx, const int64_t *m_dev, in
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = idx[q];
         const double h = st.dt[i];
+        int e = 0;
+        const bool pow2 = pow2_exponent(h, e);
         double d[6][3], A[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             double c3, c4, c5;
-            correct_component(st, i, k, h, ra[3 * q + k], rj[3 * q + k], rs[3 * q + k], c3, c4, c5, A[k]);
+            correct_component(st, i, k, h, e, pow2, ra[3 * q + k], rj[3 * q + k], rs[3 * q + k], c3, c4, c5, A[k]);
             d[0][k] = ra[3 * q + k];
             d[1][k] = rj[3 * q + k];
             d[2][k] = rs[3 * q + k];
@@ -526,7 +683,7 @@ __global__ void k_correct(State st, const int32_t *idx, const int64_t *m_dev, in
             d[4][k] = c4;
             d[5][k] = c5;
         }
-        finish_step(st, i, h, d, A, sp);
+        finish_step(st, i, h, e, pow2, d, A, sp);
     }
 }
 

@@ -116,3 +116,41 @@ def test_full_size_n1048576_mixed(hg):
         hg.hg_free(mixed)
         if f64 is not None:
             hg.hg_free(f64)
+
+
+@pytest.mark.parametrize("imf,eps", [("salpeter", 1e-4), ("equal", 0.0)])
+def test_step_choices_equal_the_fp64_criterion(hg, imf, eps):
+    """Every new step the FP64 path takes (graph-replayed block steps) equals the
+    oracle's p = 6 criterion and power-of-two rule applied to that particle's own
+    derivatives: a0, j0, s0 before the step, a1, j1, s1 after it, crackle, pop and
+    a^(5) from the oracle's interpolation.  Wide magnitude ranges: Salpeter masses
+    with eps = 1e-4, and eps = 0."""
+    import oracle
+    from paper_1207_2367_gb300 import inputs
+    n = 2048
+    p = inputs.plummer(n, 31, imf=imf)
+    o = hg.hg_default_opts(precision=hg.HG_FP64, dt_max=1.0 / 16)
+    ctx = hg.hg_init(p.mass, p.pos, p.vel, eps, 0.45, o)
+    checked = mismatch = 0
+    try:
+        before, _ = gpu_state(hg, ctx, n)
+        for _ in range(60):
+            hg.hg_step(ctx, 1)
+            after, _ = gpu_state(hg, ctx, n)
+            moved = np.nonzero(after["t"] != before["t"])[0]
+            for i in moved:
+                h = before["dt"][i]
+                c1, p1, q1 = oracle.interp(h, before["acc"][i], before["jerk"][i], before["snap"][i],
+                                           after["acc"][i], after["jerk"][i], after["snap"][i])
+                crit = oracle.criterion(0.45, 6, np.concatenate([after["acc"][i], after["jerk"][i],
+                                                                 after["snap"][i], c1, p1, q1]))
+                want = oracle.block_dt(crit, h, after["t"][i], o.dt_min, o.dt_max)
+                checked += 1
+                mismatch += int(after["dt"][i] != want)
+            before = after
+    finally:
+        hg.hg_free(ctx)
+    assert checked > 1000
+    # the GPU's FMA-contracted interpolation differs from the oracle's in the last
+    # bits; only a criterion within ~1e-15 of a power of two could decide otherwise
+    assert mismatch <= max(1, checked // 100000), (mismatch, checked)
