@@ -44,6 +44,7 @@ struct hg_ctx {
     std::vector<cudaEvent_t> ev_one, ev_many;   // profile: 6 events per captured block step
     double prof_ms[5] = {0, 0, 0, 0, 0};
     int64_t prof_steps = 0;
+    bool tnext_valid = false;   // d_sc->tnext_bits = min_i tend_i of the current state
     double t_pred = NAN;    // time of the last hg_predict (NaN: none valid)
     int64_t cur_m = -1;     // size of the block from hg_next_block (-1: none)
     int64_t eval_m = -1;    // size of the last hg_evaluate (-1: none pending)
@@ -165,7 +166,7 @@ int run_eval_host_m(hg_ctx *c, int64_t m)
         grid = c->egrid;
     }
     HG_CUDA(c, launch_eval(c->mixed, a, grid, c->stream));
-    HG_CUDA(c, launch_reduce(a, c->ra, c->rj, c->rs, c->stream));
+    HG_CUDA(c, launch_reduce(a, c->ra, c->rj, c->rs, 2 * c->num_sms, c->stream));
     c->kernels += 2;
     return HG_OK;
 }
@@ -200,7 +201,10 @@ int upload_scalar(hg_ctx *c, double *dev_field, double v)
     return HG_OK;
 }
 
-constexpr int kStepKernels = 7;   // 3 next-block passes, predict, evaluate, reduce, correct
+// Kernels per graph-replayed block step: one system, selection + prediction,
+// evaluation, reduction, correction (with the next minimum); clusters, three
+// next-block passes, batch plan, prediction, evaluation, reduction, correction.
+int step_kernels(const hg_ctx *c) { return c->bv.nc > 0 ? 8 : 4; }
 
 // An event record that becomes a graph node when the stream is being captured
 // (a plain record inside a capture only orders work and cannot be timed).
@@ -211,26 +215,42 @@ cudaError_t record_external(cudaEvent_t e, cudaStream_t s)
 
 // One block step (Table 1 sections 1-4 and 8), sizes read on the device.
 // ev: 6 events bracketing the 5 sections, or nullptr.
+// One system: the selection is fused into the prediction (the "next" section
+// is then empty) and the correction leaves the next block time, so a step is
+// four kernels and starts from d_sc->tnext_bits.
 int enqueue_block_step(hg_ctx *c, cudaStream_t s, const cudaEvent_t *ev)
 {
+    const bool batch = c->bv.nc > 0;
     if (ev) HG_CUDA(c, record_external(ev[0], s));
-    HG_CUDA(c, launch_next_block(c->st, c->n, c->nb_part, c->nb_cnt, c->nb_off, c->d_idx, c->d_sc,
-                                 c->bv.nc > 0 ? 2 : 1, c->pp, s));
-    if (c->bv.nc > 0) HG_CUDA(c, batch_plan(c, &c->d_sc->m, 0, s));
+    if (batch) {
+        HG_CUDA(c, launch_next_block(c->st, c->n, c->nb_part, c->nb_cnt, c->nb_off, c->d_idx, c->d_sc, 2, c->pp, s));
+        HG_CUDA(c, batch_plan(c, &c->d_sc->m, 0, s));
+    }
     if (ev) HG_CUDA(c, record_external(ev[1], s));
-    if (c->bv.nc > 0)
+    if (batch)
         HG_CUDA(c, launch_predict_clusters(c->mixed, c->st, c->rec, c->n, c->bv, &c->d_sc->t_cur, &c->d_sc->m, s));
     else
-        HG_CUDA(c, launch_predict(c->mixed, c->st, c->rec, c->n, c->npad, &c->d_sc->t_cur, 0.0, &c->d_sc->m, nullptr,
-                                  s));
+        HG_CUDA(c, launch_predict_select(c->mixed, c->st, c->rec, c->n, c->npad, c->d_idx, c->d_sc, 1, c->pp, s));
     if (ev) HG_CUDA(c, record_external(ev[2], s));
     EvalArgs a = eval_args(c, &c->d_sc->m, 0);
     HG_CUDA(c, launch_eval(c->mixed, a, c->egrid, s));
     if (ev) HG_CUDA(c, record_external(ev[3], s));
-    HG_CUDA(c, launch_reduce(a, c->ra, c->rj, c->rs, s));
+    HG_CUDA(c, launch_reduce(a, c->ra, c->rj, c->rs, 2 * c->num_sms, s));
     if (ev) HG_CUDA(c, record_external(ev[4], s));
-    HG_CUDA(c, launch_correct(c->st, c->d_idx, &c->d_sc->m, 0, c->n, c->ra, c->rj, c->rs, step_params(c), s));
+    HG_CUDA(c, launch_correct(c->st, c->d_idx, &c->d_sc->m, 0, c->n, c->ra, c->rj, c->rs, step_params(c), c->d_sc,
+                              batch ? 0 : 1, 2 * c->num_sms, s));
     if (ev) HG_CUDA(c, record_external(ev[5], s));
+    return HG_OK;
+}
+
+// Graph steps of one system start from d_sc->tnext_bits: compute it when the
+// state changed by other means (start-up, hg_set_state, hg_correct).
+int ensure_tnext(hg_ctx *c)
+{
+    if (c->bv.nc > 0 || c->tnext_valid) return HG_OK;
+    HG_CUDA(c, launch_next_min(c->st, c->n, c->nb_part, c->d_sc, c->stream));
+    c->kernels += 1;
+    c->tnext_valid = true;
     return HG_OK;
 }
 
@@ -270,7 +290,7 @@ int replay(hg_ctx *c, bool many)
 {
     HG_CUDA(c, cudaGraphLaunch(many ? c->g_many : c->g_one, c->stream));
     const int steps = many ? c->opts.graph_steps : 1;
-    c->kernels += (int64_t)(kStepKernels + (c->bv.nc > 0 ? 1 : 0)) * steps;
+    c->kernels += (int64_t)step_kernels(c) * steps;
     if (!c->opts.profile) return HG_OK;
     HG_CUDA(c, cudaStreamSynchronize(c->stream));
     const std::vector<cudaEvent_t> &ev = many ? c->ev_many : c->ev_one;
@@ -819,7 +839,10 @@ int hg_correct(hg_ctx *c, const int32_t *idx, int64_t m)
     if (rc) return rc;
     if (flag)
         return fail(c, HG_ESTATE, "list differs from the evaluation, or a particle is not due at the block time");
-    HG_CUDA(c, launch_correct(c->st, c->d_idx, nullptr, m, m, c->ra, c->rj, c->rs, step_params(c), c->stream));
+    const int cgrid = (int)std::min<int64_t>((m + 127) / 128, 2 * (int64_t)c->num_sms);
+    HG_CUDA(c, launch_correct(c->st, c->d_idx, nullptr, m, c->n, c->ra, c->rj, c->rs, step_params(c), c->d_sc, 0,
+                              cgrid, c->stream));
+    c->tnext_valid = false;
     c->kernels += 1;
     rc = upload_scalar(c, &c->d_sc->t_cur, c->eval_t);
     if (rc) return rc;
@@ -833,6 +856,7 @@ int hg_step(hg_ctx *c, int64_t n_steps)
     if (n_steps < 0) return fail(c, HG_EINVAL, "n_steps must be >= 0");
     if (n_steps == 0) return HG_OK;
     int rc = ensure_graphs(c);
+    if (rc == HG_OK) rc = ensure_tnext(c);
     if (rc) return rc;
     invalidate(c);
     const int64_t s = c->opts.graph_steps;
@@ -848,6 +872,7 @@ int hg_advance(hg_ctx *c, double t_end, int64_t *steps_out)
     if (!c) return HG_EINVAL;
     if (!isfinite(t_end)) return fail(c, HG_EINVAL, "t_end must be finite");
     int rc = ensure_graphs(c);
+    if (rc == HG_OK) rc = ensure_tnext(c);
     if (rc) return rc;
     invalidate(c);
     rc = sync_scalars(c);
@@ -943,6 +968,7 @@ int hg_set_state(hg_ctx *c, const hg_state *in)
     for (auto &q : g)
         HG_CUDA(c, cudaMemcpyAsync(q.dst, q.src, q.len * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     HG_CUDA(c, launch_tend(c->st, n, c->stream));
+    c->tnext_valid = false;
     rc = upload_scalar(c, &c->d_sc->t_cur, in->t_sys);
     if (rc) return rc;
     invalidate(c);

@@ -545,9 +545,9 @@ cudaError_t launch_eval(bool mixed, const EvalArgs &args, int grid, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_reduce(const EvalArgs &args, double *ra, double *rj, double *rs, cudaStream_t st)
+cudaError_t launch_reduce(const EvalArgs &args, double *ra, double *rj, double *rs, int grid, cudaStream_t st)
 {
-    k_reduce<<<1024, 256, 0, st>>>(args, ra, rj, rs);
+    k_reduce<<<grid, 256, 0, st>>>(args, ra, rj, rs);
     return cudaGetLastError();
 }
 

@@ -21,10 +21,11 @@ struct DevScalars {
     int32_t done;          // set when a next-block pass found t_next > t_stop
     int32_t err;           // error bits (ERR_*)
     int32_t flag;          // scratch result of validation kernels
-    int32_t pad;
+    uint32_t slot;         // active-list entries taken so far by the fused selection
     int64_t plan[6];       // evaluation plan of the current block (a Plan, written on the device)
-    int64_t tnext_bits;    // bit pattern of min_i tend_i (next-block pass 1)
-    uint32_t arrive[2];    // CTAs done in next-block passes 1 and 2 (the last one resets it)
+    int64_t tnext_bits;    // bit pattern of min_i tend_i (next-block pass 1, or the last correction)
+    uint32_t arrive[4];    // CTAs done in next-block passes 1 and 2 and in the fused
+                           // selection (the last one resets it); one spare
 };
 
 enum : int32_t { ERR_TIMEOUT = 1, ERR_BADIDX = 2, ERR_STATE = 4, ERR_VALUE = 8 };
@@ -216,8 +217,9 @@ void set_call_error(const char *msg);
 cudaError_t eval_setup(int device);
 int eval_grid(bool mixed, int num_sms);
 cudaError_t launch_eval(bool mixed, const EvalArgs &args, int grid, cudaStream_t st);
-// Sums the b partials of each listed particle into res_{a,j,s} [m][3].
-cudaError_t launch_reduce(const EvalArgs &args, double *ra, double *rj, double *rs, cudaStream_t st);
+// Sums the b partials of each listed particle into res_{a,j,s} [m][3]
+// (grid-stride: grid CTAs of 256 threads, a few per SM).
+cudaError_t launch_reduce(const EvalArgs &args, double *ra, double *rj, double *rs, int grid, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // PTX helpers: mbarrier and bulk (TMA) copies global -> shared.

@@ -397,6 +397,63 @@ __global__ void k_predict_clusters(const State st, const Records rec, int64_t n,
     }
 }
 
+// One system, graph-replayed block steps: Table 1 sections 1 and 2 in one
+// pass.  sc->tnext_bits holds min_i tend_i of the current state (left by the
+// previous correction).  Every thread predicts its records to t_next and the
+// due particles (tend_i == t_next, exact integer compare) are appended to idx
+// with one atomic per warp: the list order is arbitrary, which changes nothing
+// computed (a particle's sums do not depend on its position in the list).  The
+// last CTA to finish (arrival count, no waiting) publishes m, the block time,
+// the counters and the evaluation plan, and clears the minimum for the next
+// correction.  t_next > t_stop: no step (m = 0, done).
+template <bool MIXED>
+__global__ void __launch_bounds__(64) k_predict_select(const State st, const Records rec, int64_t n, int64_t npad,
+                                                       int32_t *idx, DevScalars *sc, int count_step,
+                                                       const PlanParams pq)
+{
+    __shared__ int last;
+    const long long tn = *((volatile long long *)&sc->tnext_bits);
+    const double t_next = __longlong_as_double(tn);
+    if (!(t_next <= *((volatile double *)&sc->t_stop))) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            sc->m = 0;
+            sc->done = 1;
+        }
+        return;
+    }
+    const long long *bits = reinterpret_cast<const long long *>(st.tend);
+    const int l = threadIdx.x & 31;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < npad; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        if (i < npad) predict_record<MIXED>(st, rec, i, n, i, t_next);
+        const bool due = i < n && bits[i] == tn;
+        const unsigned ball = __ballot_sync(0xffffffffu, due);
+        if (ball) {
+            uint32_t b0 = 0;
+            if (l == 0) b0 = atomicAdd(&sc->slot, (uint32_t)__popc(ball));
+            b0 = __shfl_sync(0xffffffffu, b0, 0);
+            const int64_t at = (int64_t)b0 + __popc(ball & ((1u << l) - 1u));
+            if (due) {
+                if (at < n) idx[at] = (int32_t)i;
+                else atomicOr(&sc->err, ERR_STATE);   // unreachable while slot starts at 0
+            }
+        }
+    }
+    if (!last_to_arrive(&sc->arrive[2], gridDim.x, &last)) return;
+    __threadfence();
+    const int64_t m = (int64_t)*((volatile uint32_t *)&sc->slot);
+    if (threadIdx.x == 0) {
+        sc->m = m;
+        sc->t_cur = t_next;
+        sc->done = 0;
+        sc->steps += 1;
+        if (count_step == 1) sc->interactions += m * n;
+        sc->slot = 0u;
+        sc->tnext_bits = LLONG_MAX;
+    }
+    plan_on_block(m > 0 ? m : 1, pq, sc);
+}
+
 // Predicted FP64 positions and velocities (energy diagnostics).
 __global__ void k_predict_xv(const State st, int64_t n, double tt, double *xe, double *ve)
 {
@@ -629,8 +686,8 @@ __device__ __forceinline__ double sq3(const double *p) { return p[0] * p[0] + p[
 // A: the acceleration change left after a0 + j0 h + s0 h^2/2.  Below the noise
 // floor of the evaluation (sp.noise_rel |a1|, compared as squares) the
 // interpolated derivatives are noise and the criterion may not shrink the step.
-__device__ __forceinline__ void finish_step(const State &st, int64_t i, double h, int e, bool pow2,
-                                            const double (*d)[3], const double *A, const StepParams &sp)
+__device__ __forceinline__ double finish_step(const State &st, int64_t i, double h, int e, bool pow2,
+                                              const double (*d)[3], const double *A, const StepParams &sp)
 {
     const double t1 = st.t[i] + h;
     const bool noisy = sp.noise_rel > 0.0 && sq3(A) < (sp.noise_rel * sp.noise_rel) * sq3(d[0]);
@@ -660,12 +717,17 @@ __device__ __forceinline__ void finish_step(const State &st, int64_t i, double h
     st.t[i] = t1;
     st.dt[i] = dt1;
     st.tend[i] = t1 + dt1;
+    return t1 + dt1;
 }
 
-__global__ void k_correct(State st, const int32_t *idx, const int64_t *m_dev, int64_t m_host, const double *ra,
-                          const double *rj, const double *rs, StepParams sp)
+__global__ void __launch_bounds__(128) k_correct(State st, const int32_t *idx, const int64_t *m_dev, int64_t m_host,
+                                                 const double *ra, const double *rj, const double *rs, StepParams sp,
+                                                 DevScalars *sc, int64_t n, int min_pass)
 {
+    __shared__ long long sh[32];
     const int64_t m = m_dev ? *m_dev : m_host;
+    if (m <= 0) return;
+    long long low = LLONG_MAX;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = idx[q];
         const double h = st.dt[i];
@@ -683,8 +745,22 @@ __global__ void k_correct(State st, const int32_t *idx, const int64_t *m_dev, in
             d[4][k] = c4;
             d[5][k] = c5;
         }
-        finish_step(st, i, h, e, pow2, d, A, sp);
+        low = min(low, __double_as_longlong(finish_step(st, i, h, e, pow2, d, A, sp)));
     }
+    if (!min_pass) return;
+    // Next block time: min over the new tend of the particles corrected here and
+    // over every particle whose tend differs from the block time.  A particle of
+    // the block read while another CTA corrects it shows either its old tend
+    // (== block time: skipped, its new value is in that CTA's minimum) or its new
+    // one (final): no ordering between CTAs is needed.
+    const long long tb = __double_as_longlong(*((volatile double *)&sc->t_cur));
+    const volatile long long *bits = reinterpret_cast<const volatile long long *>(st.tend);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const long long v = bits[i];
+        if (v != tb) low = min(low, v);
+    }
+    low = block_min_ll(low, sh);
+    if (threadIdx.x == 0 && low != LLONG_MAX) atomicMin((long long *)&sc->tnext_bits, low);
 }
 
 
@@ -1097,6 +1173,13 @@ cudaError_t launch_next_block(const State &st, int64_t n, double *part, int32_t 
     return cudaGetLastError();
 }
 
+cudaError_t launch_next_min(const State &st, int64_t n, double *part, DevScalars *sc, cudaStream_t s)
+{
+    const int g = nb_grid(n);
+    k_nb_min<<<g, kNBThreads, 0, s>>>(st.tend, n, kNBChunk, reinterpret_cast<long long *>(part), g, sc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tend(const State &st, int64_t n, cudaStream_t s)
 {
     k_tend<<<grid_for(n, 256, 4096), 256, 0, s>>>(st, n);
@@ -1112,6 +1195,17 @@ cudaError_t launch_predict(bool mixed, const State &st, const Records &rec, int6
         k_predict<true><<<g, 64, 0, s>>>(st, rec, n, npad, t_dev, t_host, m_dev, rmap);
     else
         k_predict<false><<<g, 64, 0, s>>>(st, rec, n, npad, t_dev, t_host, m_dev, rmap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_predict_select(bool mixed, const State &st, const Records &rec, int64_t n, int64_t npad,
+                                  int32_t *idx, DevScalars *sc, int count_step, const PlanParams &pq, cudaStream_t s)
+{
+    const int g = grid_for(npad, 64, 1 << 20);
+    if (mixed)
+        k_predict_select<true><<<g, 64, 0, s>>>(st, rec, n, npad, idx, sc, count_step, pq);
+    else
+        k_predict_select<false><<<g, 64, 0, s>>>(st, rec, n, npad, idx, sc, count_step, pq);
     return cudaGetLastError();
 }
 
@@ -1149,11 +1243,11 @@ cudaError_t launch_start(const State &st, int64_t n, const double *ra, const dou
     return cudaGetLastError();
 }
 
-cudaError_t launch_correct(const State &st, const int32_t *idx, const int64_t *m_dev, int64_t m_host, int64_t n_max,
-                           const double *ra, const double *rj, const double *rs, const StepParams &sp, cudaStream_t s)
+cudaError_t launch_correct(const State &st, const int32_t *idx, const int64_t *m_dev, int64_t m_host, int64_t n,
+                           const double *ra, const double *rj, const double *rs, const StepParams &sp,
+                           DevScalars *sc, int min_pass, int grid, cudaStream_t s)
 {
-    // One warp per CTA: the FP64 pipe is the limit, so spread small blocks over many SMs.
-    k_correct<<<grid_for(n_max, 32, 16384), 32, 0, s>>>(st, idx, m_dev, m_host, ra, rj, rs, sp);
+    k_correct<<<grid, 128, 0, s>>>(st, idx, m_dev, m_host, ra, rj, rs, sp, sc, n, min_pass);
     return cudaGetLastError();
 }
 

@@ -236,7 +236,7 @@ extern "C" int hg_evaluate_static(int64_t n, const double *mass, const double *p
     a.err = err;
     const int grid = (int)(a.plan_host.n_items < pq.grid ? a.plan_host.n_items : pq.grid);
     if (cudaGetLastError() != cudaSuccess || launch_eval(mixed, a, grid, st) != cudaSuccess ||
-        launch_reduce(a, acc, jerk, snap, st) != cudaSuccess) {
+        launch_reduce(a, acc, jerk, snap, 2 * slot->sms, st) != cudaSuccess) {
         set_call_error("launch failed");
         return HG_ECUDA;
     }
