@@ -218,12 +218,9 @@ cudaError_t record_external(cudaEvent_t e, cudaStream_t s)
 // One system: the selection is fused into the prediction (the "next" section
 // is then empty) and the correction leaves the next block time, so a step is
 // four kernels and starts from d_sc->tnext_bits.
-// Without profiling events, the four kernels of one system are programmatic
-// dependents of their predecessors (PDL); `first`: no kernel precedes in the capture.
-int enqueue_block_step(hg_ctx *c, cudaStream_t s, const cudaEvent_t *ev, bool first)
+int enqueue_block_step(hg_ctx *c, cudaStream_t s, const cudaEvent_t *ev)
 {
     const bool batch = c->bv.nc > 0;
-    const bool pdl = !batch && !ev;
     if (ev) HG_CUDA(c, record_external(ev[0], s));
     if (batch) {
         HG_CUDA(c, launch_next_block(c->st, c->n, c->nb_part, c->nb_cnt, c->nb_off, c->d_idx, c->d_sc, 2, c->pp, s));
@@ -233,16 +230,15 @@ int enqueue_block_step(hg_ctx *c, cudaStream_t s, const cudaEvent_t *ev, bool fi
     if (batch)
         HG_CUDA(c, launch_predict_clusters(c->mixed, c->st, c->rec, c->n, c->bv, &c->d_sc->t_cur, &c->d_sc->m, s));
     else
-        HG_CUDA(c, launch_predict_select(c->mixed, c->st, c->rec, c->n, c->npad, c->d_idx, c->d_sc, 1, c->pp, s,
-                                         pdl && !first));
+        HG_CUDA(c, launch_predict_select(c->mixed, c->st, c->rec, c->n, c->npad, c->d_idx, c->d_sc, 1, c->pp, s));
     if (ev) HG_CUDA(c, record_external(ev[2], s));
     EvalArgs a = eval_args(c, &c->d_sc->m, 0);
-    HG_CUDA(c, launch_eval(c->mixed, a, c->egrid, s, pdl));
+    HG_CUDA(c, launch_eval(c->mixed, a, c->egrid, s));
     if (ev) HG_CUDA(c, record_external(ev[3], s));
-    HG_CUDA(c, launch_reduce(a, c->ra, c->rj, c->rs, 2 * c->num_sms, s, pdl));
+    HG_CUDA(c, launch_reduce(a, c->ra, c->rj, c->rs, 2 * c->num_sms, s));
     if (ev) HG_CUDA(c, record_external(ev[4], s));
     HG_CUDA(c, launch_correct(c->st, c->d_idx, &c->d_sc->m, 0, c->n, c->ra, c->rj, c->rs, step_params(c), c->d_sc,
-                              batch ? 0 : 1, 2 * c->num_sms, s, pdl));
+                              batch ? 0 : 1, 2 * c->num_sms, s));
     if (ev) HG_CUDA(c, record_external(ev[5], s));
     return HG_OK;
 }
@@ -268,7 +264,7 @@ int capture(hg_ctx *c, int steps, cudaGraphExec_t *out, std::vector<cudaEvent_t>
     HG_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = HG_OK;
     for (int k = 0; k < steps && rc == HG_OK; ++k)
-        rc = enqueue_block_step(c, c->cap_stream, c->opts.profile ? &ev[(size_t)k * 6] : nullptr, k == 0);
+        rc = enqueue_block_step(c, c->cap_stream, c->opts.profile ? &ev[(size_t)k * 6] : nullptr);
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
     if (rc != HG_OK) {
         if (g) cudaGraphDestroy(g);

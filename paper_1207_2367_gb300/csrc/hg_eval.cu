@@ -294,13 +294,6 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * P::kStageBytes);
     double *red = reinterpret_cast<double *>(bars + kStages);
     const int tid = threadIdx.x;
-    if (tid == 0) {   // (touches no data of earlier kernels: may overlap them)
-#pragma unroll
-        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
-        fence_mbar_init();
-    }
-    grid_dep_wait();
-    grid_dep_trigger();
 
     const int64_t m = args.m_dev ? *args.m_dev : args.m_host;
     if (m <= 0) return;
@@ -310,6 +303,12 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
     const int64_t n_items = batch ? bv.item_off[bv.nc] : pl.n_items;
     const int64_t tps = batch ? *bv.tps : pl.tiles_per_split;
     if ((int64_t)blockIdx.x >= n_items) return;
+
+    if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
     __syncthreads();
 
     const typename P::Eps eps2 = (typename P::Eps)args.eps2;
@@ -445,8 +444,6 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
 // chunk order and scatter them to acc/jerk/snap [m][3].
 __global__ void k_reduce(const EvalArgs args, double *ra, double *rj, double *rs)
 {
-    grid_dep_wait();
-    grid_dep_trigger();
     const int64_t m = args.m_dev ? *args.m_dev : args.m_host;
     if (m <= 0) return;
     const Plan pl = args.plan_dev ? *args.plan_dev : args.plan_host;
@@ -532,19 +529,26 @@ int eval_grid(bool mixed, int num_sms)
     return (mixed ? occupancy<MixedEval, false>() : occupancy<F64, false>()) * num_sms;
 }
 
-cudaError_t launch_eval(bool mixed, const EvalArgs &args, int grid, cudaStream_t st, bool pdl)
+cudaError_t launch_eval(bool mixed, const EvalArgs &args, int grid, cudaStream_t st)
 {
-    if (mixed)
-        return launch_kernel(args.guard ? k_eval<MixedEval, true> : k_eval<MixedEval, false>, dim3(grid),
-                             dim3(kEvalThreads), smem_bytes<MixedEval>(), st, pdl, args);
-    return launch_kernel(args.guard ? k_eval<F64, true> : k_eval<F64, false>, dim3(grid), dim3(kEvalThreads),
-                         smem_bytes<F64>(), st, pdl, args);
+    if (mixed) {
+        if (args.guard)
+            k_eval<MixedEval, true><<<grid, kEvalThreads, smem_bytes<MixedEval>(), st>>>(args);
+        else
+            k_eval<MixedEval, false><<<grid, kEvalThreads, smem_bytes<MixedEval>(), st>>>(args);
+    } else {
+        if (args.guard)
+            k_eval<F64, true><<<grid, kEvalThreads, smem_bytes<F64>(), st>>>(args);
+        else
+            k_eval<F64, false><<<grid, kEvalThreads, smem_bytes<F64>(), st>>>(args);
+    }
+    return cudaGetLastError();
 }
 
-cudaError_t launch_reduce(const EvalArgs &args, double *ra, double *rj, double *rs, int grid, cudaStream_t st,
-                          bool pdl)
+cudaError_t launch_reduce(const EvalArgs &args, double *ra, double *rj, double *rs, int grid, cudaStream_t st)
 {
-    return launch_kernel(k_reduce, dim3(grid), dim3(256), 0, st, pdl, args, ra, rj, rs);
+    k_reduce<<<grid, 256, 0, st>>>(args, ra, rj, rs);
+    return cudaGetLastError();
 }
 
 // Overheads in units of one thread's j-iteration (I interactions): per tile the

@@ -216,11 +216,10 @@ void set_call_error(const char *msg);
 // Host-side launchers (hg_eval.cu).
 cudaError_t eval_setup(int device);
 int eval_grid(bool mixed, int num_sms);
-cudaError_t launch_eval(bool mixed, const EvalArgs &args, int grid, cudaStream_t st, bool pdl = false);
+cudaError_t launch_eval(bool mixed, const EvalArgs &args, int grid, cudaStream_t st);
 // Sums the b partials of each listed particle into res_{a,j,s} [m][3]
 // (grid-stride: grid CTAs of 256 threads, a few per SM).
-cudaError_t launch_reduce(const EvalArgs &args, double *ra, double *rj, double *rs, int grid, cudaStream_t st,
-                          bool pdl = false);
+cudaError_t launch_reduce(const EvalArgs &args, double *ra, double *rj, double *rs, int grid, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // PTX helpers: mbarrier and bulk (TMA) copies global -> shared.
@@ -290,16 +289,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
-// Programmatic dependent launch: a kernel launched with
-// cudaLaunchAttributeProgrammaticStreamSerialization may start while the
-// previous kernel of the stream is still running.  grid_dep_wait() returns once
-// that kernel has completed and its writes are visible; kernels that use it call
-// it before reading anything an earlier kernel wrote and before any exit, so the
-// ordering stays transitive.  Without the attribute it returns at once.
-// grid_dep_trigger() lets the next kernel's CTAs be scheduled early.
-__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void grid_dep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
 // Hardware reciprocal square root (single MUFU instruction, flush-to-zero).
 __device__ __forceinline__ float rsqrt_approx(float x)
 {
@@ -308,26 +297,5 @@ __device__ __forceinline__ float rsqrt_approx(float x)
     return y;
 }
 #endif
-
-// Kernel launch, optionally as a programmatic dependent of the previous kernel
-// of the stream (the kernel must begin with grid_dep_wait()).
-template <typename... KArgs, typename... Args>
-cudaError_t launch_kernel(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
-                          Args... args)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    if (pdl) {
-        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        at[0].val.programmaticStreamSerializationAllowed = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-    }
-    return cudaLaunchKernelEx(&cfg, k, args...);
-}
 
 }  // namespace hg

@@ -412,8 +412,6 @@ __global__ void __launch_bounds__(64) k_predict_select(const State st, const Rec
                                                        const PlanParams pq)
 {
     __shared__ int last;
-    grid_dep_wait();
-    grid_dep_trigger();
     const long long tn = *((volatile long long *)&sc->tnext_bits);
     const double t_next = __longlong_as_double(tn);
     if (!(t_next <= *((volatile double *)&sc->t_stop))) {
@@ -727,8 +725,6 @@ __global__ void __launch_bounds__(128) k_correct(State st, const int32_t *idx, c
                                                  DevScalars *sc, int64_t n, int min_pass)
 {
     __shared__ long long sh[32];
-    grid_dep_wait();
-    grid_dep_trigger();
     const int64_t m = m_dev ? *m_dev : m_host;
     if (m <= 0) return;
     long long low = LLONG_MAX;
@@ -1203,12 +1199,14 @@ cudaError_t launch_predict(bool mixed, const State &st, const Records &rec, int6
 }
 
 cudaError_t launch_predict_select(bool mixed, const State &st, const Records &rec, int64_t n, int64_t npad,
-                                  int32_t *idx, DevScalars *sc, int count_step, const PlanParams &pq, cudaStream_t s,
-                                  bool pdl)
+                                  int32_t *idx, DevScalars *sc, int count_step, const PlanParams &pq, cudaStream_t s)
 {
     const int g = grid_for(npad, 64, 1 << 20);
-    return launch_kernel(mixed ? k_predict_select<true> : k_predict_select<false>, dim3(g), dim3(64), 0, s, pdl, st,
-                         rec, n, npad, idx, sc, count_step, pq);
+    if (mixed)
+        k_predict_select<true><<<g, 64, 0, s>>>(st, rec, n, npad, idx, sc, count_step, pq);
+    else
+        k_predict_select<false><<<g, 64, 0, s>>>(st, rec, n, npad, idx, sc, count_step, pq);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_predict_clusters(bool mixed, const State &st, const Records &rec, int64_t n, const BatchView &bv,
@@ -1247,10 +1245,10 @@ cudaError_t launch_start(const State &st, int64_t n, const double *ra, const dou
 
 cudaError_t launch_correct(const State &st, const int32_t *idx, const int64_t *m_dev, int64_t m_host, int64_t n,
                            const double *ra, const double *rj, const double *rs, const StepParams &sp,
-                           DevScalars *sc, int min_pass, int grid, cudaStream_t s, bool pdl)
+                           DevScalars *sc, int min_pass, int grid, cudaStream_t s)
 {
-    return launch_kernel(k_correct, dim3(grid), dim3(128), 0, s, pdl, st, idx, m_dev, m_host, ra, rj, rs, sp, sc, n,
-                         min_pass);
+    k_correct<<<grid, 128, 0, s>>>(st, idx, m_dev, m_host, ra, rj, rs, sp, sc, n, min_pass);
+    return cudaGetLastError();
 }
 
 int energy_splits(int64_t n, int num_sms)

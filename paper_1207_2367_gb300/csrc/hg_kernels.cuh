@@ -27,8 +27,7 @@ cudaError_t launch_next_min(const State &st, int64_t n, double *part, DevScalars
 // min_pass); predicts every record to t_next, lists the due particles in idx
 // (arbitrary order), sets m, t_cur, done, the counters and the plan.
 cudaError_t launch_predict_select(bool mixed, const State &st, const Records &rec, int64_t n, int64_t npad,
-                                  int32_t *idx, DevScalars *sc, int count_step, const PlanParams &pq, cudaStream_t s,
-                                  bool pdl = false);
+                                  int32_t *idx, DevScalars *sc, int count_step, const PlanParams &pq, cudaStream_t s);
 // tend = t + dt after the state was replaced.
 cudaError_t launch_tend(const State &st, int64_t n, cudaStream_t s);
 // rmap: record of each particle (clusters), or nullptr (record i = particle i).
@@ -54,7 +53,7 @@ cudaError_t launch_start(const State &st, int64_t n, const double *ra, const dou
 // selection).  grid: CTAs of 128 threads.
 cudaError_t launch_correct(const State &st, const int32_t *idx, const int64_t *m_dev, int64_t m_host, int64_t n,
                            const double *ra, const double *rj, const double *rs, const StepParams &sp,
-                           DevScalars *sc, int min_pass, int grid, cudaStream_t s, bool pdl = false);
+                           DevScalars *sc, int min_pass, int grid, cudaStream_t s);
 int energy_splits(int64_t n, int num_sms);
 cudaError_t launch_energy(bool mixed, const State &st, int64_t n, double t, double eps2, double *xe, double *ve,
                           double *phi_part, int nsplit, double *part2, int g2, double *out2, const BatchView &bv,
