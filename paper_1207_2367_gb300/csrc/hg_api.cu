@@ -22,7 +22,7 @@ struct hg_ctx {
     bool mixed = false;
     double eps = 0.0, eta = 0.0;
     hg_opts opts{};
-    int device = 0, num_sms = 0, egrid = 0;
+    int device = 0, num_sms = 0;
     cudaStream_t stream = nullptr, cap_stream = nullptr;
     bool own_stream = false;
     State st{}, st2{};
@@ -159,13 +159,11 @@ cudaError_t batch_plan(hg_ctx *c, const int64_t *m_dev, int64_t m_host, cudaStre
 int run_eval_host_m(hg_ctx *c, int64_t m)
 {
     EvalArgs a = eval_args(c, nullptr, m);
-    int grid = (int)(a.plan_host.n_items < c->egrid ? a.plan_host.n_items : c->egrid);
     if (c->bv.nc > 0) {
         HG_CUDA(c, batch_plan(c, nullptr, m, c->stream));
         c->kernels += 1;
-        grid = c->egrid;
     }
-    HG_CUDA(c, launch_eval(c->mixed, a, grid, c->stream));
+    HG_CUDA(c, launch_eval(c->mixed, a, c->num_sms, c->stream));
     HG_CUDA(c, launch_reduce(a, c->ra, c->rj, c->rs, 2 * c->num_sms, c->stream));
     c->kernels += 2;
     return HG_OK;
@@ -202,9 +200,10 @@ int upload_scalar(hg_ctx *c, double *dev_field, double v)
 }
 
 // Kernels per graph-replayed block step: one system, selection + prediction,
-// evaluation, reduction, correction (with the next minimum); clusters, three
-// next-block passes, batch plan, prediction, evaluation, reduction, correction.
-int step_kernels(const hg_ctx *c) { return c->bv.nc > 0 ? 8 : 4; }
+// evaluation (mixed: both kernel variants, one returns at once), reduction,
+// correction (with the next minimum); clusters, three next-block passes, batch
+// plan, prediction, evaluation, reduction, correction.
+int step_kernels(const hg_ctx *c) { return c->bv.nc > 0 ? 8 : (c->mixed ? 5 : 4); }
 
 // An event record that becomes a graph node when the stream is being captured
 // (a plain record inside a capture only orders work and cannot be timed).
@@ -233,7 +232,7 @@ int enqueue_block_step(hg_ctx *c, cudaStream_t s, const cudaEvent_t *ev)
         HG_CUDA(c, launch_predict_select(c->mixed, c->st, c->rec, c->n, c->npad, c->d_idx, c->d_sc, 1, c->pp, s));
     if (ev) HG_CUDA(c, record_external(ev[2], s));
     EvalArgs a = eval_args(c, &c->d_sc->m, 0);
-    HG_CUDA(c, launch_eval(c->mixed, a, c->egrid, s));
+    HG_CUDA(c, launch_eval(c->mixed, a, c->num_sms, s));
     if (ev) HG_CUDA(c, record_external(ev[3], s));
     HG_CUDA(c, launch_reduce(a, c->ra, c->rj, c->rs, 2 * c->num_sms, s));
     if (ev) HG_CUDA(c, record_external(ev[4], s));
@@ -451,8 +450,8 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
     if (!ok) return fail(c, HG_ENOMEM, "device allocation failed");
 
     HG_CUDA(c, eval_setup(c->device));
-    c->egrid = eval_grid(c->mixed, c->num_sms);
     c->pp = plan_params(c->mixed, c->npad, c->num_sms, c->pcap, c->opts.tpi, c->opts.jsplit);
+    if (nc > 0) c->pp.variants = 1;   // the cluster work list is built for the first kernel variant
 
     DevScalars z{};
     z.t_stop = INFINITY;
@@ -497,7 +496,7 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
 // ---------------------------------------------------------------------------
 // Autotuning of the evaluation plan per block-size bucket.
 // ---------------------------------------------------------------------------
-constexpr int kTuneCand = 12;        // cheapest plans of the cost model timed per bucket
+constexpr int kTuneCand = 14;        // cheapest plans of the cost model timed per bucket
 constexpr double kTuneGain = 0.97;   // a rival is stored only if at least 3% faster
 constexpr double kTuneTargetUs = 2000.0;
 
@@ -544,26 +543,27 @@ std::vector<int> tune_candidates(const hg_ctx *c, int64_t m)
     for (int k = 0; k < kTuneBuckets; ++k) q.tuned[k] = -1;
     struct Cand {
         int64_t cost;
-        int c, tpi, b;
+        int c, tpi, b, v;
     };
     std::vector<Cand> all;
-    for (int k = 0; k < kPlanCandidates; ++k) {
+    for (int k = 0; k < plan_total(q); ++k) {
         Plan p;
         const int64_t cost = plan_candidate(m, q, k, p);
         if (cost < 0) continue;
         bool dup = false;
-        for (const Cand &x : all) dup = dup || (x.tpi == p.tpi && x.b == p.b);
-        if (!dup) all.push_back(Cand{cost, k, p.tpi, p.b});
+        for (const Cand &x : all) dup = dup || (x.tpi == p.tpi && x.b == p.b && x.v == p.variant);
+        if (!dup) all.push_back(Cand{cost, k, p.tpi, p.b, p.variant});
     }
     std::stable_sort(all.begin(), all.end(), [](const Cand &a, const Cand &b) { return a.cost < b.cost; });
     std::vector<bool> take(all.size(), false);
     for (size_t k = 0; k < all.size() && (int)k < kTuneCand; ++k) take[k] = true;
-    for (int t = 1; t <= kMaxTPI; t *= 2)
-        for (size_t k = 0; k < all.size(); ++k)
-            if (all[k].tpi == t) {
-                take[k] = true;
-                break;
-            }
+    for (int v = 0; v < q.variants; ++v)
+        for (int t = 1; t <= kMaxTPI; t *= 2)
+            for (size_t k = 0; k < all.size(); ++k)
+                if (all[k].tpi == t && all[k].v == v) {
+                    take[k] = true;
+                    break;
+                }
     for (size_t k = 0; k < all.size(); ++k)
         if (take[k]) out.push_back(all[k].c);
     return out;
@@ -1027,7 +1027,7 @@ int hg_set_tuning(hg_ctx *c, const int16_t *table)
     if (!c || !table) return HG_EINVAL;
     for (int k = 0; k < kTuneBuckets; ++k) {
         const int v = table[k];
-        const bool ok = v == -1 || (c->bv.nc > 0 ? batch_code_ok(v) : (v >= 0 && v < kPlanCandidates));
+        const bool ok = v == -1 || (c->bv.nc > 0 ? batch_code_ok(v) : (v >= 0 && v < plan_total(c->pp)));
         if (!ok) return fail(c, HG_EINVAL, "tuning table value out of range for this context");
     }
     for (int k = 0; k < kTuneBuckets; ++k) c->pp.tuned[k] = table[k];

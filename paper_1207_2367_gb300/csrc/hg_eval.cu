@@ -24,10 +24,16 @@ constexpr int kFold = 32;   // FP32 pair sums are folded into the compensated su
 // Mixed precision: FP32 pair arithmetic, double-single position differences,
 // Kahan-compensated FP32 sums (Sect. 5.7 hybrid precision, redesigned).
 // ------------------------------------------------------------------------
+// IPT i-particles per thread: 2 with 4 CTAs per SM (128 registers) for small
+// and medium blocks, 3 with 2 CTAs per SM for large ones (more independent
+// pair chains per warp and fewer shared-memory loads per pair; ~9 % more pairs
+// per second at m = N, but a longer latency for small blocks).
+template <int IPT>
 struct Mixed {
     static constexpr int TJ = kTJMixed;
-    static constexpr int I = kIMixed;
-    static constexpr int kMinBlocks = 4;
+    static constexpr int I = IPT;
+    static constexpr int kMinBlocks = IPT == kIMixed ? 4 : 2;
+    static constexpr int kVariant = IPT == kIMixed ? 0 : 1;
     static constexpr uint32_t kStageBytes = TJ * 52;
     struct IData {
         float xh, yh, zh, xl, yl, zl, vx, vy, vz, ax, ay, az;
@@ -174,6 +180,7 @@ struct F64 {
     static constexpr int TJ = kTJF64;
     static constexpr int I = kIF64;
     static constexpr int kMinBlocks = 2;
+    static constexpr int kVariant = 0;
     static constexpr uint32_t kStageBytes = TJ * 80;
     struct IData {
         double x, y, z, vx, vy, vz, ax, ay, az;
@@ -278,7 +285,8 @@ struct F64 {
     }
 };
 
-typedef Mixed MixedEval;
+typedef Mixed<kIMixed> MixedEval;
+typedef Mixed<kIMixedWide> MixedWide;
 
 template <class P>
 constexpr size_t smem_bytes()
@@ -300,6 +308,7 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
     const BatchView &bv = args.bv;
     const bool batch = bv.nc > 0;
     const Plan pl = args.plan_dev ? *args.plan_dev : args.plan_host;
+    if (!batch && pl.variant != P::kVariant) return;   // the plan runs on the other kernel
     const int64_t n_items = batch ? bv.item_off[bv.nc] : pl.n_items;
     const int64_t tps = batch ? *bv.tps : pl.tiles_per_split;
     if ((int64_t)blockIdx.x >= n_items) return;
@@ -520,6 +529,8 @@ cudaError_t eval_setup(int)
     cudaError_t e;
     if ((e = set_attr<MixedEval, false>()) != cudaSuccess) return e;
     if ((e = set_attr<MixedEval, true>()) != cudaSuccess) return e;
+    if ((e = set_attr<MixedWide, false>()) != cudaSuccess) return e;
+    if ((e = set_attr<MixedWide, true>()) != cudaSuccess) return e;
     if ((e = set_attr<F64, false>()) != cudaSuccess) return e;
     return set_attr<F64, true>();
 }
@@ -529,20 +540,40 @@ int eval_grid(bool mixed, int num_sms)
     return (mixed ? occupancy<MixedEval, false>() : occupancy<F64, false>()) * num_sms;
 }
 
-cudaError_t launch_eval(bool mixed, const EvalArgs &args, int grid, cudaStream_t st)
+namespace {
+template <class P>
+cudaError_t launch_one(const EvalArgs &args, int grid, cudaStream_t st)
 {
-    if (mixed) {
-        if (args.guard)
-            k_eval<MixedEval, true><<<grid, kEvalThreads, smem_bytes<MixedEval>(), st>>>(args);
-        else
-            k_eval<MixedEval, false><<<grid, kEvalThreads, smem_bytes<MixedEval>(), st>>>(args);
-    } else {
-        if (args.guard)
-            k_eval<F64, true><<<grid, kEvalThreads, smem_bytes<F64>(), st>>>(args);
-        else
-            k_eval<F64, false><<<grid, kEvalThreads, smem_bytes<F64>(), st>>>(args);
-    }
+    if (args.guard)
+        k_eval<P, true><<<grid, kEvalThreads, smem_bytes<P>(), st>>>(args);
+    else
+        k_eval<P, false><<<grid, kEvalThreads, smem_bytes<P>(), st>>>(args);
     return cudaGetLastError();
+}
+
+template <class P>
+int clip_grid(const EvalArgs &args, int num_sms)
+{
+    const int64_t full = (int64_t)occupancy<P, false>() * num_sms;
+    if (args.plan_dev || args.bv.nc > 0) return (int)full;
+    const int64_t items = args.plan_host.n_items;
+    return (int)(items < full ? (items > 0 ? items : 1) : full);
+}
+}  // namespace
+
+int eval_launches(bool mixed, const EvalArgs &args) { return (mixed && args.bv.nc == 0) ? 2 : 1; }
+
+cudaError_t launch_eval(bool mixed, const EvalArgs &args, int num_sms, cudaStream_t st)
+{
+    if (!mixed) return launch_one<F64>(args, clip_grid<F64>(args, num_sms), st);
+    const bool batch = args.bv.nc > 0;
+    if (batch) return launch_one<MixedEval>(args, clip_grid<MixedEval>(args, num_sms), st);
+    if (!args.plan_dev)
+        return args.plan_host.variant == 1 ? launch_one<MixedWide>(args, clip_grid<MixedWide>(args, num_sms), st)
+                                           : launch_one<MixedEval>(args, clip_grid<MixedEval>(args, num_sms), st);
+    cudaError_t e = launch_one<MixedEval>(args, clip_grid<MixedEval>(args, num_sms), st);
+    if (e != cudaSuccess) return e;
+    return launch_one<MixedWide>(args, clip_grid<MixedWide>(args, num_sms), st);
 }
 
 cudaError_t launch_reduce(const EvalArgs &args, double *ra, double *rj, double *rs, int grid, cudaStream_t st)
@@ -567,6 +598,15 @@ PlanParams plan_params(bool mixed, int64_t npad, int num_sms, int64_t pcap, int 
     q.b_force = b_force;
     q.c_tile = mixed ? 2 : 1;
     q.c_item = mixed ? 24 : 2;
+    // Mixed: the large-block kernel holds 3 i-particles per thread on half the
+    // threads per SM.  Its SMs evaluate ~9 % more pairs per second at m = N, so
+    // one of its thread iterations (3 pairs, 256 threads per SM) takes about
+    // (3 * 256) / (2 * 512) / 1.09 = 0.69 of a variant-0 iteration.
+    q.variants = mixed ? 2 : 1;
+    q.ipt1 = MixedWide::I;
+    q.grid1 = mixed ? occupancy<MixedWide, false>() * num_sms : q.grid;
+    q.weight1 = 69;
+    q.weight1_one = 130;
     for (int k = 0; k < kTuneBuckets; ++k) q.tuned[k] = -1;
     return q;
 }

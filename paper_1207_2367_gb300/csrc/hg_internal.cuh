@@ -53,7 +53,8 @@ constexpr int kEvalThreads = 128;
 constexpr int kStages = 3;
 constexpr int kTJMixed = 256;   // j-records per shared-memory tile, mixed
 constexpr int kTJF64 = 128;     // j-records per shared-memory tile, fp64
-constexpr int kIMixed = 2;      // i-particles held per thread, mixed
+constexpr int kIMixed = 2;      // i-particles held per thread, mixed, small-block variant
+constexpr int kIMixedWide = 3;  // the same, large-block variant (fewer, register-heavier CTAs)
 constexpr int kIF64 = 1;        // i-particles held per thread, fp64
 constexpr int kMaxTPI = 64;
 constexpr double kPadCoord = 1.0e18;
@@ -68,19 +69,26 @@ constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 // of its arguments: the evaluation and the reduction compute the same plan.
 // ---------------------------------------------------------------------------
 struct Plan {
-    int tpi, ti, b, pad;
+    int tpi, ti, b, variant;   // variant: which evaluation kernel runs the plan
     int64_t n_itiles, tiles_per_split, n_items;
 };
 
 constexpr int kTuneBuckets = HG_TUNE_BUCKETS;   // block sizes 2^k <= m < 2^(k+1)
 
-// Inputs of the planner that do not change between block steps.
+// Inputs of the planner that do not change between block steps.  Variant 0
+// holds i_per_thread particles per thread on `grid` persistent CTAs; variant 1
+// (mixed, one system) holds ipt1 on grid1 CTAs.  One of its j-iterations costs
+// weight1 / 100 of a variant-0 iteration when the plan needs several waves of
+// work items (throughput-bound), weight1_one / 100 when one wave holds them all
+// (latency-bound: a thread's longer iteration is not hidden by other warps).
 struct PlanParams {
     int64_t ntiles;      // j-tiles of npad records
     int64_t pcap;        // b * m <= pcap (partial-sum capacity)
     int i_per_thread, tj, grid;
     int tpi_force, b_force;
     int c_tile, c_item;  // per-tile and per-item overhead, in j-iterations of one thread
+    int variants;        // 1 or 2 evaluation kernels to choose from
+    int ipt1, grid1, weight1, weight1_one;
     // Measured choices per block-size bucket (-1: cost model).  One system: a
     // candidate index; clusters: a batch code (see batch_knobs).
     int16_t tuned[kTuneBuckets];
@@ -93,9 +101,10 @@ __host__ __device__ inline int tune_bucket(int64_t m)
     return k;
 }
 
-// Candidate c in [0, kPlanCandidates): threads per i = 2^(c / 32), tiles per
-// split from kTps[c % 32].
+// Candidate c in [0, variants * kPlanCandidates): variant c / kPlanCandidates,
+// threads per i = 2^((c % kPlanCandidates) / 32), tiles per split plan_tps(c % 32).
 constexpr int kPlanCandidates = 7 * 32;
+constexpr int kPlanVariantsMax = 2;
 __host__ __device__ inline int64_t plan_tps(int k)
 {
     const int64_t t[32] = {1,  2,  3,  4,  5,  6,   7,   8,   9,   10,  11,   12,   13,   14,   15,   16,
@@ -108,6 +117,10 @@ __host__ __device__ inline int64_t plan_tps(int k)
 // so that host and device choose the same plan.
 __host__ __device__ inline int64_t plan_candidate(int64_t m, const PlanParams &q, int c, Plan &p)
 {
+    const int v = c / kPlanCandidates;
+    if (c < 0 || v >= q.variants) return -1;
+    c -= v * kPlanCandidates;
+    const int ipt = v ? q.ipt1 : q.i_per_thread, grid = v ? q.grid1 : q.grid;
     const int tpi = 1 << (c / 32);
     if (tpi > kMaxTPI || (q.tpi_force > 0 && tpi != q.tpi_force)) return -1;
     int64_t tps = plan_tps(c % 32);
@@ -121,15 +134,18 @@ __host__ __device__ inline int64_t plan_candidate(int64_t m, const PlanParams &q
     const int64_t mm = m > 0 ? m : 1;
     if (b * mm > q.pcap && b > 1) return -1;
     p.tpi = tpi;
-    p.ti = kEvalThreads / tpi * q.i_per_thread;
+    p.ti = kEvalThreads / tpi * ipt;
     p.n_itiles = (mm + p.ti - 1) / p.ti;
     p.tiles_per_split = tps;
     p.b = (int)b;
-    p.pad = 0;
+    p.variant = v;
     p.n_items = p.n_itiles * b;
-    const int64_t waves = (p.n_items + q.grid - 1) / q.grid;
-    return waves * (tps * (q.tj / tpi + q.c_tile) + q.c_item);
+    const int64_t waves = (p.n_items + grid - 1) / grid;
+    const int64_t w = v == 0 ? 100 : (waves > 1 ? q.weight1 : q.weight1_one);
+    return waves * (tps * ((q.tj / tpi) * w + q.c_tile * 100) + q.c_item * 100);
 }
+
+__host__ __device__ inline int plan_total(const PlanParams &q) { return q.variants * kPlanCandidates; }
 
 // The tuned candidate of m's bucket if there is one and it is admissible, else
 // the cheapest admissible candidate of the cost model (ties: lowest index).
@@ -137,9 +153,9 @@ __host__ __device__ inline Plan make_plan(int64_t m, const PlanParams &q)
 {
     Plan best{}, p{};
     const int tc = q.tuned[tune_bucket(m)];
-    if (tc >= 0 && tc < kPlanCandidates && plan_candidate(m, q, tc, p) >= 0) return p;
+    if (tc >= 0 && plan_candidate(m, q, tc, p) >= 0) return p;
     int64_t best_cost = -1;
-    for (int c = 0; c < kPlanCandidates; ++c) {
+    for (int c = 0; c < plan_total(q); ++c) {
         const int64_t cost = plan_candidate(m, q, c, p);
         if (cost >= 0 && (best_cost < 0 || cost < best_cost)) {
             best_cost = cost;
@@ -216,7 +232,13 @@ void set_call_error(const char *msg);
 // Host-side launchers (hg_eval.cu).
 cudaError_t eval_setup(int device);
 int eval_grid(bool mixed, int num_sms);
-cudaError_t launch_eval(bool mixed, const EvalArgs &args, int grid, cudaStream_t st);
+// Evaluation of args.  Host plan: the plan's kernel variant on min(items, its
+// grid) CTAs (clusters: variant 0 on its full grid).  Device plan (graph steps):
+// every variant of the precision on its full grid; the ones the plan does not
+// name return at once.
+cudaError_t launch_eval(bool mixed, const EvalArgs &args, int num_sms, cudaStream_t st);
+// Kernels launch_eval issues for a device plan.
+int eval_launches(bool mixed, const EvalArgs &args);
 // Sums the b partials of each listed particle into res_{a,j,s} [m][3]
 // (grid-stride: grid CTAs of 256 threads, a few per SM).
 cudaError_t launch_reduce(const EvalArgs &args, double *ra, double *rj, double *rs, int grid, cudaStream_t st);

@@ -64,13 +64,13 @@ __device__ void plan_on_block(int64_t m, const PlanParams &q, DevScalars *sc)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
     Plan p;
     const int tc = q.tuned[tune_bucket(m)];
-    if (tc >= 0 && tc < kPlanCandidates && plan_candidate(m, q, tc, p) >= 0) {   // measured choice
+    if (tc >= 0 && plan_candidate(m, q, tc, p) >= 0) {   // measured choice
         if (threadIdx.x == 0) *reinterpret_cast<Plan *>(sc->plan) = p;
         return;
     }
     int64_t best = -1;
     int bc = 0x7fffffff;
-    for (int c = threadIdx.x; c < kPlanCandidates; c += blockDim.x) {
+    for (int c = threadIdx.x; c < plan_total(q); c += blockDim.x) {
         const int64_t cost = plan_candidate(m, q, c, p);
         if (cost >= 0 && (best < 0 || cost < best)) {
             best = cost;

@@ -234,8 +234,7 @@ extern "C" int hg_evaluate_static(int64_t n, const double *mass, const double *p
     a.guard = eps == 0.0 ? 1 : 0;
     a.tx_extra = 0;
     a.err = err;
-    const int grid = (int)(a.plan_host.n_items < pq.grid ? a.plan_host.n_items : pq.grid);
-    if (cudaGetLastError() != cudaSuccess || launch_eval(mixed, a, grid, st) != cudaSuccess ||
+    if (cudaGetLastError() != cudaSuccess || launch_eval(mixed, a, slot->sms, st) != cudaSuccess ||
         launch_reduce(a, acc, jerk, snap, 2 * slot->sms, st) != cudaSuccess) {
         set_call_error("launch failed");
         return HG_ECUDA;

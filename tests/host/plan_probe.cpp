@@ -21,6 +21,11 @@ int main(int argc, char **argv)
     q.b_force = 0;
     q.c_tile = 2;
     q.c_item = 24;
+    q.variants = 2;   // mixed: 2 and 3 i-particles per thread
+    q.ipt1 = hg::kIMixedWide;
+    q.grid1 = 2 * 152;
+    q.weight1 = 69;
+    q.weight1_one = 130;
     long long m;
     int v;
     while (scanf("%lld %d", &m, &v) == 2) {
@@ -30,8 +35,8 @@ int main(int argc, char **argv)
         q.tuned[b] = (int16_t)v;
         const hg::Plan p = hg::make_plan(m, q);
         const hg::BatchKnobs kn = hg::batch_knobs(m, q);
-        printf("%d %d %lld %d %lld %d %d %d\n", b, model.tpi, (long long)model.tiles_per_split, p.tpi,
-               (long long)p.tiles_per_split, p.b, kn.w_log, kn.tpi_shift);
+        printf("%d %d %lld %d %lld %d %d %d %d %d %d\n", b, model.tpi, (long long)model.tiles_per_split, p.tpi,
+               (long long)p.tiles_per_split, p.b, kn.w_log, kn.tpi_shift, p.variant, p.ti, model.variant);
     }
     return 0;
 }

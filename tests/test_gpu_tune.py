@@ -147,9 +147,33 @@ def test_tune_rejects_bad_arguments(hg):
     try:
         with pytest.raises(hg.HGError):
             hg.hg_tune(ctx, reps=-1)
-        for bad in (224, -2, 5000):
+        for bad in (448, -2, 5000):   # mixed: two kernel variants, plans [0, 448)
             with pytest.raises(hg.HGError):
                 hg.hg_set_tuning(ctx, np.full(hg.HG_TUNE_BUCKETS, bad, dtype=np.int16))
         assert np.all(hg.hg_get_tuning(ctx) == -1)
+    finally:
+        hg.hg_free(ctx)
+    ctx = gpu_context(hg, sysm, 0, EPS)
+    try:
+        with pytest.raises(hg.HGError):   # FP64: one kernel, plans [0, 224)
+            hg.hg_set_tuning(ctx, np.full(hg.HG_TUNE_BUCKETS, 224, dtype=np.int16))
+    finally:
+        hg.hg_free(ctx)
+
+
+@pytest.mark.parametrize("code", [0, 70, 165, 224, 224 + 33, 224 + 131, 224 + 194])
+def test_forced_table_matches_oracle_mixed(hg, code):
+    """Both mixed kernel variants (2 and 3 i-particles per thread) under forced
+    plans: the mixed tolerances against the oracle."""
+    n = 1000
+    sysm = oracle_system(n, 75, EPS, steps=2)
+    ctx = gpu_context(hg, sysm, 1, EPS)
+    try:
+        hg.hg_set_tuning(ctx, np.full(hg.HG_TUNE_BUCKETS, code, dtype=np.int16))
+        t = sysm.t_sys + 1.0 / 128
+        for idx in _lists(n, np.random.default_rng(code)):
+            got = gpu_eval(hg, ctx, idx, t)
+            i32 = idx.astype(np.int32)
+            check_eval(got, sysm.predict_eval(t, i32), 1, sysm.predict_absum(t, i32))
     finally:
         hg.hg_free(ctx)
