@@ -5,5 +5,5 @@ benchmark's CPU-baseline leg.  The CUDA product path never imports it.
 """
 from .oracle import (  # noqa: F401
     build, lib, predict, evaluate, eval_absum, correct, interp, criterion, block_dt, block_dt_init,
-    next_block, energy, System,
+    next_block, energy, angular_momentum, System,
 )

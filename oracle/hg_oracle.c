@@ -247,6 +247,22 @@ void or_energy(int64_t n, const double *mass, const double *x, const double *v, 
     *potential = W;
 }
 
+/* Total angular momentum L = sum_i m_i r_i x v_i, the quantity whose magnitude
+ * Sect. 5.1 checks for conservation (Delta L_k). */
+void or_angular_momentum(int64_t n, const double *mass, const double *x, const double *v, double *L)
+{
+    double Lx = 0.0, Ly = 0.0, Lz = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double *r = x + 3 * i, *u = v + 3 * i;
+        Lx += mass[i] * (r[1] * u[2] - r[2] * u[1]);
+        Ly += mass[i] * (r[2] * u[0] - r[0] * u[2]);
+        Lz += mass[i] * (r[0] * u[1] - r[1] * u[0]);
+    }
+    L[0] = Lx;
+    L[1] = Ly;
+    L[2] = Lz;
+}
+
 /* ------------------------------------------------------------------------- */
 /* The whole integrator: Sect. 3 items 1-3 repeated block by block.           */
 /* ------------------------------------------------------------------------- */
@@ -421,6 +437,13 @@ void or_sys_energy(or_sys *sy, double t, double *kinetic, double *potential)
 {
     or_predict(sy->n, sy->x, sy->v, sy->a, sy->j, sy->s, sy->c, sy->t, t, sy->xp, sy->vp, sy->ap);
     or_energy(sy->n, sy->m, sy->xp, sy->vp, sy->eps, kinetic, potential);
+}
+
+/* Angular momentum of the system predicted to time t. */
+void or_sys_angular_momentum(or_sys *sy, double t, double *L)
+{
+    or_predict(sy->n, sy->x, sy->v, sy->a, sy->j, sy->s, sy->c, sy->t, t, sy->xp, sy->vp, sy->ap);
+    or_angular_momentum(sy->n, sy->m, sy->xp, sy->vp, L);
 }
 
 /* Predict every particle to t and evaluate the listed particles (state injection checks). */

@@ -40,7 +40,9 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
+            # HG_ORACLE_LIB: a separately built copy (the planted-mistake test
+            # points the pins at a deliberately broken build this way).
+            L = C.CDLL(os.environ.get("HG_ORACLE_LIB") or build())
             L.or_predict.argtypes = [_I64] + [_D] * 7 + [C.c_double] + [_D] * 3
             L.or_eval.argtypes = [_I64, _D, _D, _D, _D, C.c_double, _I64, _I32, _D, _D, _D]
             L.or_eval_absum.argtypes = [_I64, _D, _D, _D, _D, C.c_double, _I64, _I32, _D]
@@ -55,6 +57,10 @@ def lib():
             L.or_next_block.argtypes = [_I64, _D, _D, _D, _I32]
             L.or_next_block.restype = _I64
             L.or_energy.argtypes = [_I64, _D, _D, _D, C.c_double, _D, _D]
+            L.or_angular_momentum.argtypes = [_I64, _D, _D, _D, _D]
+            L.or_angular_momentum.restype = None
+            L.or_sys_angular_momentum.argtypes = [C.c_void_p, C.c_double, _D]
+            L.or_sys_angular_momentum.restype = None
             L.or_sys_create.argtypes = [_I64, _D, _D, _D] + [C.c_double] * 5
             L.or_sys_create.restype = C.c_void_p
             L.or_sys_alloc.argtypes = [_I64] + [C.c_double] * 5
@@ -175,6 +181,15 @@ def energy(mass, x, v, eps):
     return K.value, W.value
 
 
+def angular_momentum(mass, x, v):
+    """Total angular momentum sum_i m_i r_i x v_i (3-vector)."""
+    mass = _f64(mass)
+    x, v = _f64(x, (-1, 3)), _f64(v, (-1, 3))
+    L = np.empty(3)
+    lib().or_angular_momentum(mass.shape[0], _d(mass), _d(x), _d(v), _d(L))
+    return L
+
+
 class System:
     """The oracle integrator (start-up evaluation included unless state= is given)."""
 
@@ -213,6 +228,11 @@ class System:
         K, W = C.c_double(), C.c_double()
         lib().or_sys_energy(self._p, float(self.t_sys if t is None else t), C.byref(K), C.byref(W))
         return K.value, W.value
+
+    def angular_momentum(self, t=None):
+        L = np.empty(3)
+        lib().or_sys_angular_momentum(self._p, float(self.t_sys if t is None else t), _d(L))
+        return L
 
     def predict_eval(self, t, idx):
         idx = np.ascontiguousarray(idx, dtype=np.int32)

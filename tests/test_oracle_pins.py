@@ -265,6 +265,38 @@ def test_energy_conservation_plummer_1024():
 
 
 # --------------------------------------------------------------------------
+# Angular momentum (Sect. 5.1 conservation check): hand value, the rigid-body
+# identity L = I omega, and the Kepler orbit's closed form and conservation.
+# --------------------------------------------------------------------------
+def test_angular_momentum_two_body_by_hand():
+    m = np.array([0.25, 0.75])
+    x = np.array([[0.0, 0.0, 0.0], [3.0, 4.0, 0.0]])
+    v = np.array([[1.0, 0.0, 0.0], [0.0, 2.0, 0.0]])
+    # 0.75 * (3, 4, 0) x (0, 2, 0) = 0.75 * (0, 0, 6)
+    np.testing.assert_allclose(oracle.angular_momentum(m, x, v), [0.0, 0.0, 4.5], rtol=0, atol=1e-15)
+
+
+def test_angular_momentum_rigid_rotation_is_inertia_times_omega():
+    p = inputs.plummer(500, 7)
+    omega = np.array([0.3, -1.1, 0.7])
+    v = np.cross(omega, p.pos)                 # rigid rotation about the origin
+    r2 = np.einsum("ij,ij->i", p.pos, p.pos)
+    inertia = np.einsum("i,jk->jk", p.mass * r2, np.eye(3)) - np.einsum("i,ij,ik->jk", p.mass, p.pos, p.pos)
+    np.testing.assert_allclose(oracle.angular_momentum(p.mass, p.pos, v), inertia @ omega, rtol=1e-13)
+
+
+def test_angular_momentum_kepler_closed_form_and_conservation():
+    e, a = 0.5, 1.0
+    p = inputs.kepler_pair(e=e, a=a)
+    mu = p.mass[0] * p.mass[1] / p.mass.sum()
+    L0 = oracle.angular_momentum(p.mass, p.pos, p.vel)
+    np.testing.assert_allclose(L0, [0.0, 0.0, mu * math.sqrt(p.mass.sum() * a * (1 - e * e))], rtol=1e-14)
+    s = oracle.System(p.mass, p.pos, p.vel, 0.0, 0.1, eta_init=0.1 / 45, dt_max=1.0)
+    s.advance(8.0)
+    assert np.linalg.norm(s.angular_momentum() - L0) / np.linalg.norm(L0) < 1e-10
+
+
+# --------------------------------------------------------------------------
 # Whole integrator: Kepler orbit, 6th-order convergence.
 # --------------------------------------------------------------------------
 def test_kepler_integration_sixth_order():
