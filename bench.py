@@ -47,7 +47,7 @@ EVAL_TRAFFIC = {(65536, "equal", "mixed"): 3.47e6}
 
 
 def parse_defaults():
-    return {"n": 65536, "imf": "equal", "seed": 2}
+    return {"n": 65536, "imf": "equal", "seed": 2, "t_end": 0.125}
 
 
 def parse():
@@ -70,11 +70,15 @@ def parse():
     ap.add_argument("--batch", action="store_true",
                     help="independent-clusters workload: batched context vs one context per cluster")
     ap.add_argument("--clusters", type=int, default=512)
-    ap.add_argument("--mode", choices=["interval", "batch", "block-sizes", "accuracy", "large"], default="interval",
+    ap.add_argument("--t-end", type=float, default=0.125, help="block-sizes mode: integrate from 0 to this time")
+    ap.add_argument("--precisions", default="fp64,mixed", help="block-sizes / eta-sweep modes: which paths")
+    ap.add_argument("--mode", choices=["interval", "batch", "block-sizes", "accuracy", "large", "eta-sweep"],
+                    default="interval",
                     help="interval: the default line; batch: 512 clusters; block-sizes: evaluation time per "
                          "block-size bucket, FP64 and mixed, N = 65536 to t = 1/8; accuracy: N = 2^20 Salpeter, "
                          "mixed vs FP64 per block step and |dE/E| of both; large: N = 2^23 Salpeter, 32 block "
-                         "steps including the start-up evaluation")
+                         "steps including the start-up evaluation; eta-sweep: energy and angular-momentum "
+                         "errors against eta (N = 16384, both paths)")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the cost model's launch plans (no hg_tune before the warm-up)")
     return ap.parse_args()
@@ -525,9 +529,11 @@ def _rel_stats(got, ref):
 
 
 def run_block_sizes(a):
-    """Evaluation time of every block size that occurs from t = 0 to 1/8 on the
-    N = 65536 Plummer sphere (eps 1e-4), FP64 and mixed, grouped in power-of-two
-    buckets of m; CUDA events around each graph-replayed evaluation."""
+    """Evaluation time of every block size that occurs from t = 0 to --t-end
+    (default 1/8) on the Plummer sphere of --n particles (default 65536, eps
+    1e-4), for the paths in --precisions, grouped in power-of-two buckets of m;
+    CUDA events around each section of every graph-replayed block step.  Also
+    the paper's block-group attribution H_G (Sect. 5.5) per section."""
     import torch
     from paper_1207_2367_gb300 import binding as hg
     from paper_1207_2367_gb300 import inputs
@@ -539,16 +545,19 @@ def run_block_sizes(a):
     p = inputs.plummer(a.n, a.seed, imf=a.imf)
     out = {"metric": "evaluation time per block-size bucket", "unit": "us",
            "config": {"workload": f"Plummer N={a.n}, {a.imf} masses (seed {a.seed}), eps={a.eps:g}, eta=0.45, "
-                                  "dt_max=1/16, t = 0 -> 1/8, every block step"}}
-    for prec, name in ((hg.HG_FP64, "fp64"), (hg.HG_MIXED, "mixed")):
+                                  f"dt_max=1/16, t = 0 -> {a.t_end:g}, every block step"}}
+    wanted = {"fp64": hg.HG_FP64, "mixed": hg.HG_MIXED}
+    for name in [x for x in a.precisions.split(",") if x]:
+        prec = wanted[name]
         ctx = make_ctx(hg, p, a, prec, stream, 0)
         tuning = tune(hg, ctx, a)
-        buckets = {}
+        buckets, groups = {}, {}
+        total_ms = 0.0
         hg.hg_get_profile(ctx, reset=True)
         while True:
             hg.hg_step(ctx, 1)
             st = hg.hg_get_stats(ctx)
-            if st["t_sys"] > 0.125:
+            if st["t_sys"] > a.t_end:
                 break
             pr = hg.hg_get_profile(ctx, reset=True)["ms"]
             m = st["last_m"]
@@ -557,6 +566,12 @@ def run_block_sizes(a):
             b["m_sum"] += m
             b["eval_ms"] += pr["evaluate"] + pr["reduce"]
             b["step_ms"] += sum(pr.values())
+            g = groups.setdefault(paper_group(m), {"steps": 0, "m_sum": 0, **{k: 0.0 for k in pr}})
+            g["steps"] += 1
+            g["m_sum"] += m
+            for k, v in pr.items():
+                g[k] += v
+            total_ms += sum(pr.values())
         hg.hg_free(ctx)
         peak = fp64_peak_tflops(mhz) if prec == hg.HG_FP64 else fp32_peak_tflops(mhz)
         rows = []
@@ -569,7 +584,79 @@ def run_block_sizes(a):
                          "step_us": 1e3 * b["step_ms"] / b["steps"], "interactions_per_s": rate,
                          "gflops_77": rate * 77 / 1e9, "gflops_paper_97": rate * PAPER_FLOPS / 1e9,
                          "frac_of_peak": rate * 77 / 1e12 / peak})
-        out[name] = {"buckets": rows, "peak_tflops": peak, "tuning": tuning}
+        # H_G (Sect. 5.5): share of the total time spent in block steps whose size
+        # falls in group G, per section (sections 5-7 and 9 of the paper's Table 1,
+        # host copies and MPI, do not exist here; section 1 runs inside the
+        # prediction kernel of one system).
+        hgroups = []
+        for gname in sorted(groups):
+            g = groups[gname]
+            hgroups.append({"group": gname, "range": PAPER_GROUPS[gname], "steps": g["steps"],
+                            "mean_m": g["m_sum"] / g["steps"],
+                            "H_G_percent": {k: 100.0 * g[k] / total_ms for k in ("next", "predict", "evaluate",
+                                                                              "reduce", "correct")},
+                            "H_G_total_percent": 100.0 * sum(g[k] for k in ("next", "predict", "evaluate",
+                                                                          "reduce", "correct")) / total_ms})
+        out[name] = {"buckets": rows, "groups": hgroups, "total_ms": total_ms, "peak_tflops": peak,
+                     "tuning": tuning}
+    print(json.dumps(out), flush=True)
+
+
+# The paper's block-size groups of Sect. 5.5 (bounds overlap in the text at 1k,
+# 10k, 100k; read as half-open from below).
+PAPER_GROUPS = {"A": [1, 20], "B": [21, 100], "C": [101, 1000], "D": [1001, 10000], "E": [10001, 100000],
+                "F": [100001, 1 << 40]}
+
+
+def paper_group(m):
+    for g, (lo, hi) in PAPER_GROUPS.items():
+        if lo <= m <= hi:
+            return g
+    return "F"
+
+
+def run_eta_sweep(a):
+    """Sect. 5.1 accuracy test: |dE/E| and ||L| - |L0|| / |L0| at ten equally
+    spaced synchronisation times, averaged (Delta E_k, Delta L_k), against eta,
+    for both paths; Plummer N (default 16384), equal masses, eps 1e-4,
+    dt_max = 1/16, integrated to --t-end (default 2.5, synchronisation every 0.25)."""
+    import torch
+    from paper_1207_2367_gb300 import binding as hg
+    from paper_1207_2367_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    hg.load()
+    stream = torch.cuda.Stream()
+    n = a.n
+    p = inputs.plummer(n, a.seed, imf=a.imf)
+    T = a.t_end
+    etas = (0.15, 0.3, 0.45, 0.6, 0.8, 1.0)
+    wanted = {"fp64": hg.HG_FP64, "mixed": hg.HG_MIXED}
+    out = {"metric": "energy and angular-momentum errors against eta (Sect. 5.1)",
+           "config": {"workload": f"Plummer N={n}, {a.imf} masses (seed {a.seed}), eps={a.eps:g}, dt_max=1/16, "
+                                  f"t = 0 -> {T:g}, errors at t_i = i {T / 10:g}, i = 1..10; FP64 energy sums"}}
+    for name in [x for x in a.precisions.split(",") if x]:
+        rows = []
+        for eta in etas:
+            o = hg.hg_default_opts(precision=wanted[name], energy_precision=hg.HG_FP64, dt_max=1.0 / 16,
+                                   stream=stream)
+            ctx = hg.hg_init(p.mass, p.pos, p.vel, a.eps, eta, o)
+            E0 = sum(hg.hg_energy(ctx))
+            L0 = float(np.linalg.norm(hg.hg_angular_momentum(ctx)))
+            dE, dL = [], []
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            for i in range(1, 11):
+                hg.hg_advance(ctx, i * T / 10)
+                dE.append(abs((sum(hg.hg_energy(ctx)) - E0) / E0))
+                dL.append(abs(float(np.linalg.norm(hg.hg_angular_momentum(ctx))) - L0) / L0)
+            wall = time.perf_counter() - w0
+            st = hg.hg_get_stats(ctx)
+            hg.hg_free(ctx)
+            rows.append({"eta": eta, "dE_k": float(np.mean(dE)), "dL_k": float(np.mean(dL)),
+                         "dE_max": float(np.max(dE)), "dL_max": float(np.max(dL)), "block_steps": st["block_steps"],
+                         "interactions": st["interactions"], "wall_s": wall, "L0": L0, "E0": E0})
+        out[name] = rows
     print(json.dumps(out), flush=True)
 
 
@@ -710,10 +797,12 @@ def main():
     if a.batch or a.mode == "batch":
         run_batch(a)
         return
-    modes = {"block-sizes": run_block_sizes, "accuracy": run_accuracy, "large": run_large}
+    modes = {"block-sizes": run_block_sizes, "accuracy": run_accuracy, "large": run_large,
+             "eta-sweep": run_eta_sweep}
     if a.mode in modes:
         defaults = {"accuracy": dict(n=1 << 20, imf="salpeter", seed=3),
-                    "large": dict(n=1 << 23, imf="salpeter", seed=5)}.get(a.mode, {})
+                    "large": dict(n=1 << 23, imf="salpeter", seed=5),
+                    "eta-sweep": dict(n=16384, t_end=2.5)}.get(a.mode, {})
         for k, v in defaults.items():
             if getattr(a, k) == parse_defaults()[k]:
                 setattr(a, k, v)

@@ -165,6 +165,12 @@ int hg_advance(hg_ctx *ctx, double t_end, int64_t *steps_out);
  * buffers: a pending hg_predict/hg_evaluate stays valid.  Synchronizes. */
 int hg_energy(hg_ctx *ctx, double *kinetic, double *potential);
 
+/* Total angular momentum L = sum_i m_i r_i x v_i (L[3], host) of the system
+ * predicted to the last block time, summed in FP64 in a fixed order: the
+ * quantity whose magnitude Sect. 5.1 follows for conservation.  Uses its own
+ * buffers like hg_energy.  Synchronizes. */
+int hg_angular_momentum(hg_ctx *ctx, double *L);
+
 /* Copy the state out (every non-NULL field) / replace it (every field required).
  * hg_set_state checks: masses > 0, finite values, dt a power of two in
  * [dt_min, dt_max], t_i >= 0 and a multiple of dt_i; it invalidates any

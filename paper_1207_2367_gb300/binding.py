@@ -100,12 +100,13 @@ def load(path: str | None = None):
         L.hg_free.restype = None
         L.hg_evaluate_static.argtypes = [I64, P, P, P, P, D, C.c_int32, I32P, I64, P, P, P, P]
         L.hg_evaluate_static.restype = C.c_int
+        L.hg_angular_momentum.argtypes = [P, C.POINTER(D)]
         L.hg_tune.argtypes = [P, I64, C.c_int32, C.POINTER(hg_tune_entry), C.c_int32, C.POINTER(C.c_int32)]
         L.hg_get_tuning.argtypes = [P, C.POINTER(C.c_int16)]
         L.hg_set_tuning.argtypes = [P, C.POINTER(C.c_int16)]
         for name in ("hg_init", "hg_next_block", "hg_predict", "hg_evaluate", "hg_correct", "hg_step",
                      "hg_advance", "hg_energy", "hg_get_state", "hg_set_state", "hg_get_stats", "hg_get_profile",
-                     "hg_tune", "hg_get_tuning", "hg_set_tuning"):
+                     "hg_tune", "hg_get_tuning", "hg_set_tuning", "hg_angular_momentum"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -206,6 +207,12 @@ def hg_energy(ctx):
     K, W = C.c_double(), C.c_double()
     _check(ctx, load().hg_energy(ctx, C.byref(K), C.byref(W)))
     return K.value, W.value
+
+
+def hg_angular_momentum(ctx):
+    L = (C.c_double * 3)()
+    _check(ctx, load().hg_angular_momentum(ctx, L))
+    return np.array(list(L))
 
 
 def hg_get_state(ctx, out: dict):

@@ -38,6 +38,7 @@ struct hg_ctx {
     std::vector<int64_t> cl_off_host;
     double *ra = nullptr, *rj = nullptr, *rs = nullptr;
     double *xe = nullptr, *ve = nullptr, *phi_part = nullptr, *e_part = nullptr, *e_out = nullptr;
+    double *l_part = nullptr, *l_out = nullptr;   // angular momentum: 3 partials per CTA, result
     int e_splits = 0, e_g2 = 0;
     cudaGraphExec_t g_one = nullptr, g_many = nullptr;
     int64_t kernels = 0;            // kernel launches issued (graph replays count every node)
@@ -445,8 +446,10 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
     c->e_g2 = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
     c->e_part = dalloc<double>(c, 2 * c->e_g2);
     c->e_out = dalloc<double>(c, 2);
+    c->l_part = dalloc<double>(c, 3 * c->e_g2);
+    c->l_out = dalloc<double>(c, 3);
     ok = ok && c->d_idx && c->d_idx2 && c->nb_part && c->nb_cnt && c->nb_off && c->d_sc && c->partial && c->ra && c->rj &&
-         c->rs && c->xe && c->ve && c->phi_part && c->e_part && c->e_out;
+         c->rs && c->xe && c->ve && c->phi_part && c->e_part && c->e_out && c->l_part && c->l_out;
     if (!ok) return fail(c, HG_ENOMEM, "device allocation failed");
 
     HG_CUDA(c, eval_setup(c->device));
@@ -908,6 +911,20 @@ int hg_energy(hg_ctx *c, double *kinetic, double *potential)
     HG_CUDA(c, cudaStreamSynchronize(c->stream));
     if (kinetic) *kinetic = c->h_stage[0];
     if (potential) *potential = c->h_stage[1];
+    return HG_OK;
+}
+
+int hg_angular_momentum(hg_ctx *c, double *L)
+{
+    if (!c || !L) return HG_EINVAL;
+    int rc = sync_scalars(c);
+    if (rc) return rc;
+    c->kernels += 3;
+    HG_CUDA(c, launch_angular_momentum(c->st, c->n, c->h_sc->t_cur, c->xe, c->ve, c->l_part, c->e_g2, c->l_out,
+                                       c->stream));
+    HG_CUDA(c, cudaMemcpyAsync(c->h_stage, c->l_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    HG_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 3; ++k) L[k] = c->h_stage[k];
     return HG_OK;
 }
 

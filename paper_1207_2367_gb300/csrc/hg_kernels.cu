@@ -903,6 +903,44 @@ __global__ void k_energy_final(const double *part2, int g, double *out)
     }
 }
 
+// Total angular momentum sum_i m_i r_i x v_i of the predicted system (the
+// conservation check of Sect. 5.1): per-CTA FP64 partial sums in a fixed
+// order, then one thread adds the g partials in CTA order (deterministic).
+__global__ void k_angmom_sum(const double *mass, const double *xe, const double *ve, int64_t n, double *part3)
+{
+    __shared__ double sh[3][32];
+    double L[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double *r = xe + 3 * i, *u = ve + 3 * i;
+        L[0] += mass[i] * (r[1] * u[2] - r[2] * u[1]);
+        L[1] += mass[i] * (r[2] * u[0] - r[0] * u[2]);
+        L[2] += mass[i] * (r[0] * u[1] - r[1] * u[0]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        for (int off = 16; off > 0; off >>= 1) L[c] += __shfl_xor_sync(0xffffffffu, L[c], off);
+    const int wp = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0)
+        for (int c = 0; c < 3; ++c) sh[c][wp] = L[c];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 3; ++c) {
+            double t = 0.0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[c][k];
+            part3[3 * blockIdx.x + c] = t;
+        }
+}
+
+__global__ void k_angmom_final(const double *part3, int g, double *out3)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0)
+        for (int c = 0; c < 3; ++c) {
+            double t = 0.0;
+            for (int k = 0; k < g; ++k) t += part3[3 * k + c];
+            out3[c] = t;
+        }
+}
+
 // ------------------------------------------------------------------------
 // Validation (flags, never traps).
 // ------------------------------------------------------------------------
@@ -1280,6 +1318,15 @@ cudaError_t launch_energy(bool mixed, const State &st, int64_t n, double t, doub
     }
     k_energy_sum<<<g2, 256, 0, s>>>(st.mass, ve, phi_part, n, nsplit, part2);
     k_energy_final<<<1, 32, 0, s>>>(part2, g2, out2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_angular_momentum(const State &st, int64_t n, double t, double *xe, double *ve, double *part3,
+                                    int g, double *out3, cudaStream_t s)
+{
+    k_predict_xv<<<grid_for(n, 256, 1 << 20), 256, 0, s>>>(st, n, t, xe, ve);
+    k_angmom_sum<<<g, 256, 0, s>>>(st.mass, xe, ve, n, part3);
+    k_angmom_final<<<1, 32, 0, s>>>(part3, g, out3);
     return cudaGetLastError();
 }
 

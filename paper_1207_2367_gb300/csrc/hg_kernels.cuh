@@ -58,6 +58,9 @@ int energy_splits(int64_t n, int num_sms);
 cudaError_t launch_energy(bool mixed, const State &st, int64_t n, double t, double eps2, double *xe, double *ve,
                           double *phi_part, int nsplit, double *part2, int g2, double *out2, const BatchView &bv,
                           cudaStream_t s);
+// L = sum_i m_i r_i x v_i of the system predicted to t, into out3 (part3: 3 g doubles).
+cudaError_t launch_angular_momentum(const State &st, int64_t n, double t, double *xe, double *ve, double *part3,
+                                    int g, double *out3, cudaStream_t s);
 cudaError_t launch_validate_init(const double *mass, const double *x, const double *v, int64_t n, int32_t *flag,
                                  cudaStream_t s);
 cudaError_t launch_validate_state(const State &st, int64_t n, double dt_min, double dt_max, int32_t *flag,

@@ -259,6 +259,28 @@ def test_energy_matches_oracle(hg):
             hg.hg_free(ctx)
 
 
+def test_angular_momentum_matches_oracle(hg):
+    """L of the predicted system at the last block time (oracle state injected;
+    particles at their own times), against the oracle's sum, relative to the
+    condition scale sum_i m_i |r_i| |v_i| (|L| of an isotropic Plummer sphere is
+    a near cancellation).  Plus conservation along 60 graph block steps."""
+    n, eps = 3000, 1e-3
+    sysm = oracle_system(n, 22, eps, steps=5)
+    ref = sysm.angular_momentum()
+    st = sysm.get_state()
+    scale = float(np.sum(st["mass"] * np.linalg.norm(st["pos"], axis=1) * np.linalg.norm(st["vel"], axis=1)))
+    for prec in (0, 1):
+        ctx = gpu_context(hg, sysm, prec, eps)
+        try:
+            L = hg.hg_angular_momentum(ctx)
+            assert np.linalg.norm(L - ref) <= 1e-14 * scale, (L, ref)
+            hg.hg_step(ctx, 60)
+            L1 = hg.hg_angular_momentum(ctx)
+            assert np.linalg.norm(L1 - ref) <= (1e-11 if prec == 0 else 1e-9) * scale
+        finally:
+            hg.hg_free(ctx)
+
+
 def test_kepler_orbit_zero_softening(hg):
     """Two bodies, eps = 0, e = 0.5: the GPU integrator follows the closed-form orbit."""
     p = inputs.kepler_pair()
