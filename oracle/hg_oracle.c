@@ -28,6 +28,8 @@
  *      most x2 per step and only when the new time is a multiple of the
  *      doubled step; clamp to [dt_min, dt_max];
  *  R8  the potential energy is -sum_{i<j} m_i m_j / sqrt(r_ij^2 + eps^2).
+ * Besides the paper's 6th-order scheme the integrator offers the 4th-order
+ * Hermite scheme its criterion admits with p = 4 (or_correct4, or_interp4).
  */
 #include <math.h>
 #include <stdint.h>
@@ -169,6 +171,35 @@ void or_interp(double h, const double *a0, const double *j0, const double *s0, c
     }
 }
 
+/* 4th-order variant (the paper's criterion with p = 4): the two-point Hermite
+ * corrector of the standard 4th-order Hermite scheme (Makino & Aarseth 1992),
+ * from a and jerk at both ends of the step:
+ *   v1 = v0 + h/2 (a0 + a1) + h^2/12 (j0 - j1),
+ *   x1 = x0 + h/2 (v0 + v1) + h^2/12 (a0 - a1). */
+void or_correct4(double h, const double *x0, const double *v0, const double *a0, const double *j0,
+                 const double *a1, const double *j1, double *x1, double *v1)
+{
+    for (int k = 0; k < 3; ++k) {
+        v1[k] = v0[k] + h / 2.0 * (a0[k] + a1[k]) + h * h / 12.0 * (j0[k] - j1[k]);
+        x1[k] = x0[k] + h / 2.0 * (v0[k] + v1[k]) + h * h / 12.0 * (a0[k] - a1[k]);
+    }
+}
+
+/* The cubic a(tau) on [0, h] matching a and jerk at both ends: its 3rd
+ * derivative (crackle, constant) is c = (12 (a0 - a1) + 6 h (j0 + j1)) / h^3 and
+ * its 2nd derivative (snap) at tau = 0 is (-6 (a0 - a1) - h (4 j0 + 2 j1)) / h^2;
+ * s1 = snap at tau = h = s0 + c h. */
+void or_interp4(double h, const double *a0, const double *j0, const double *a1, const double *j1,
+                double *s1, double *c1)
+{
+    for (int k = 0; k < 3; ++k) {
+        double c = (12.0 * (a0[k] - a1[k]) + 6.0 * h * (j0[k] + j1[k])) / (h * h * h);
+        double s0 = (-6.0 * (a0[k] - a1[k]) - h * (4.0 * j0[k] + 2.0 * j1[k])) / (h * h);
+        s1[k] = s0 + c * h;
+        c1[k] = c;
+    }
+}
+
 /* Sect. 3, generalized Aarseth criterion: dt = eta (A^(1) / A^(p-2))^(1/(p-3)),
  * A^(s) = sqrt(|a^(s-1)| |a^(s+1)| + |a^(s)|^2).  deriv holds a^(0) .. a^(p-1)
  * as p consecutive 3-vectors.  A^(p-2) = 0 gives +inf (no limit). */
@@ -268,6 +299,7 @@ void or_angular_momentum(int64_t n, const double *mass, const double *x, const d
 /* ------------------------------------------------------------------------- */
 typedef struct or_sys {
     int64_t n;
+    int order;                                     /* 6 (the paper's scheme) or 4 */
     double eps, eta, eta_init, dt_min, dt_max, t_sys;
     int64_t steps, interactions;
     double *m, *x, *v, *a, *j, *s, *c, *t, *dt;   /* state at each particle's own time */
@@ -319,6 +351,7 @@ or_sys *or_sys_alloc(int64_t n, double eps, double eta, double eta_init, double 
     sy->eta_init = eta_init;
     sy->dt_min = dt_min;
     sy->dt_max = dt_max;
+    sy->order = 6;
     size_t s1 = (size_t)n * sizeof(double), s3 = 3 * s1;
     sy->m = malloc(s1); sy->t = malloc(s1); sy->dt = malloc(s1);
     sy->x = malloc(s3); sy->v = malloc(s3); sy->a = malloc(s3); sy->j = malloc(s3);
@@ -337,12 +370,13 @@ or_sys *or_sys_alloc(int64_t n, double eps, double eta, double eta_init, double 
 /* Start-up: all particles active at t = 0 (prediction is the identity), one full
  * evaluation, crackle = 0 and the first step from the p = 4 criterion with
  * eta_init (Reading R6). */
-or_sys *or_sys_create(int64_t n, const double *mass, const double *pos, const double *vel, double eps,
-                      double eta, double eta_init, double dt_min, double dt_max)
+or_sys *or_sys_create_order(int64_t n, const double *mass, const double *pos, const double *vel, double eps,
+                            double eta, double eta_init, double dt_min, double dt_max, int order)
 {
     or_sys *sy = or_sys_alloc(n, eps, eta, eta_init, dt_min, dt_max);
     if (!sy)
         return NULL;
+    sy->order = order;
     memcpy(sy->m, mass, (size_t)n * sizeof(double));
     memcpy(sy->x, pos, 3 * (size_t)n * sizeof(double));
     memcpy(sy->v, vel, 3 * (size_t)n * sizeof(double));
@@ -364,11 +398,18 @@ or_sys *or_sys_create(int64_t n, const double *mass, const double *pos, const do
         memset(d + 9, 0, 3 * sizeof(double));
         memcpy(sy->a + 3 * i, d + 0, 3 * sizeof(double));
         memcpy(sy->j + 3 * i, d + 3, 3 * sizeof(double));
-        memcpy(sy->s + 3 * i, d + 6, 3 * sizeof(double));
+        if (order == 6)   /* the 4th-order scheme keeps a and jerk only */
+            memcpy(sy->s + 3 * i, d + 6, 3 * sizeof(double));
         sy->dt[i] = or_block_dt_init(or_criterion(eta_init, 4, d), dt_min, dt_max);
     }
     sy->t_sys = 0.0;
     return sy;
+}
+
+or_sys *or_sys_create(int64_t n, const double *mass, const double *pos, const double *vel, double eps,
+                      double eta, double eta_init, double dt_min, double dt_max)
+{
+    return or_sys_create_order(n, mass, pos, vel, eps, eta, eta_init, dt_min, dt_max, 6);
 }
 
 /* Corrector, interpolation and new step for the m listed particles whose step
@@ -380,6 +421,23 @@ static void or_sys_finish(or_sys *sy, int64_t m, double t_now)
         double h = sy->dt[i];
         double *a1 = sy->ra + 3 * q, *j1 = sy->rj + 3 * q, *s1 = sy->rs + 3 * q;
         double x1[3], v1[3], d[18];
+        if (sy->order == 4) {
+            /* 4th-order scheme: corrector from a and jerk, snap and crackle at the
+             * step's end from the cubic interpolant, the p = 4 criterion; the
+             * stored snap and crackle stay zero (the predictor ends at jerk). */
+            or_correct4(h, sy->x + 3 * i, sy->v + 3 * i, sy->a + 3 * i, sy->j + 3 * i, a1, j1, x1, v1);
+            memcpy(d + 0, a1, 3 * sizeof(double));
+            memcpy(d + 3, j1, 3 * sizeof(double));
+            or_interp4(h, sy->a + 3 * i, sy->j + 3 * i, a1, j1, d + 6, d + 9);
+            double crit4 = or_criterion(sy->eta, 4, d);
+            memcpy(sy->x + 3 * i, x1, 3 * sizeof(double));
+            memcpy(sy->v + 3 * i, v1, 3 * sizeof(double));
+            memcpy(sy->a + 3 * i, a1, 3 * sizeof(double));
+            memcpy(sy->j + 3 * i, j1, 3 * sizeof(double));
+            sy->t[i] = t_now;
+            sy->dt[i] = or_block_dt(crit4, h, t_now, sy->dt_min, sy->dt_max);
+            continue;
+        }
         or_correct(h, sy->x + 3 * i, sy->v + 3 * i, sy->a + 3 * i, sy->j + 3 * i, sy->s + 3 * i,
                    a1, j1, s1, x1, v1);
         or_interp(h, sy->a + 3 * i, sy->j + 3 * i, sy->s + 3 * i, a1, j1, s1, d + 9, d + 12, d + 15);
@@ -481,6 +539,7 @@ int or_sys_set(or_sys *sy, int field, const double *in)
     return 0;
 }
 
+void or_sys_set_order(or_sys *sy, int order) { sy->order = order; }
 double or_sys_time(const or_sys *sy) { return sy->t_sys; }
 void or_sys_set_time(or_sys *sy, double t) { sy->t_sys = t; }
 int64_t or_sys_steps(const or_sys *sy) { return sy->steps; }

@@ -62,6 +62,14 @@ def lib():
             L.or_sys_angular_momentum.argtypes = [C.c_void_p, C.c_double, _D]
             L.or_sys_angular_momentum.restype = None
             L.or_sys_create.argtypes = [_I64, _D, _D, _D] + [C.c_double] * 5
+            L.or_sys_create_order.argtypes = [_I64, _D, _D, _D] + [C.c_double] * 5 + [C.c_int]
+            L.or_sys_create_order.restype = C.c_void_p
+            L.or_sys_set_order.argtypes = [C.c_void_p, C.c_int]
+            L.or_sys_set_order.restype = None
+            L.or_correct4.argtypes = [C.c_double] + [_D] * 8
+            L.or_correct4.restype = None
+            L.or_interp4.argtypes = [C.c_double] + [_D] * 6
+            L.or_interp4.restype = None
             L.or_sys_create.restype = C.c_void_p
             L.or_sys_alloc.argtypes = [_I64] + [C.c_double] * 5
             L.or_sys_alloc.restype = C.c_void_p
@@ -141,6 +149,22 @@ def correct(h, x0, v0, a0, j0, s0, a1, j1, s1):
     return x1, v1
 
 
+def correct4(h, x0, v0, a0, j0, a1, j1):
+    """4th-order Hermite corrector: (x1, v1)."""
+    args = [_f64(q, (3,)) for q in (x0, v0, a0, j0, a1, j1)]
+    x1, v1 = np.empty(3), np.empty(3)
+    lib().or_correct4(float(h), *[_d(q) for q in args], _d(x1), _d(v1))
+    return x1, v1
+
+
+def interp4(h, a0, j0, a1, j1):
+    """snap and crackle at the end of a step from the cubic Hermite interpolant."""
+    args = [_f64(q, (3,)) for q in (a0, j0, a1, j1)]
+    s1, c1 = np.empty(3), np.empty(3)
+    lib().or_interp4(float(h), *[_d(q) for q in args], _d(s1), _d(c1))
+    return s1, c1
+
+
 def interp(h, a0, j0, s0, a1, j1, s1):
     """crackle, pop and 5th derivative at the end of a step from the Hermite interpolant."""
     args = [_f64(q, (3,)) for q in (a0, j0, s0, a1, j1, s1)]
@@ -194,17 +218,21 @@ class System:
     """The oracle integrator (start-up evaluation included unless state= is given)."""
 
     def __init__(self, mass, pos, vel, eps, eta, eta_init=0.01, dt_min=2.0 ** -25, dt_max=2.0 ** -3,
-                 state=None):
+                 state=None, order=6):
         L = lib()
         mass = _f64(mass)
         self.n = mass.shape[0]
+        if order not in (4, 6):
+            raise ValueError("order must be 4 or 6")
         if state is None:
             pos, vel = _f64(pos, (-1, 3)), _f64(vel, (-1, 3))
-            self._p = L.or_sys_create(self.n, _d(mass), _d(pos), _d(vel), float(eps), float(eta),
-                                      float(eta_init), float(dt_min), float(dt_max))
+            self._p = L.or_sys_create_order(self.n, _d(mass), _d(pos), _d(vel), float(eps), float(eta),
+                                            float(eta_init), float(dt_min), float(dt_max), int(order))
         else:
             self._p = L.or_sys_alloc(self.n, float(eps), float(eta), float(eta_init), float(dt_min),
                                      float(dt_max))
+            if self._p:
+                L.or_sys_set_order(self._p, int(order))
         if not self._p:
             raise MemoryError("oracle allocation failed")
         if state is not None:

@@ -191,6 +191,58 @@ def test_interpolation_exact_for_quintic_acceleration():
     assert rel(q1, _poly(ca, h, 5)) < 1e-8
 
 
+@pytest.mark.parametrize("deg_x,exact_v,exact_x", [(4, True, True), (5, True, False), (6, False, False)])
+def test_corrector4_exactness(deg_x, exact_v, exact_x):
+    """4th-order corrector (two-point Hermite quadrature, exact for cubic
+    integrands): v exact when a(t) has degree <= 3, x when x(t) has degree <= 4."""
+    coef = rng.normal(size=(deg_x + 1, 3))
+    h = 0.375
+    x0, v0, a0, j0 = (_poly(coef, 0.0, k) for k in range(4))
+    a1, j1 = (_poly(coef, h, k) for k in (2, 3))
+    x1, v1 = oracle.correct4(h, x0, v0, a0, j0, a1, j1)
+    ev, ex = rel(v1, _poly(coef, h, 1)), rel(x1, _poly(coef, h, 0))
+    assert (ev < 1e-13) == exact_v, ev
+    assert (ex < 1e-13) == exact_x, ex
+
+
+def test_interpolation4_exact_for_cubic_acceleration():
+    ca = rng.normal(size=(4, 3))       # a(t) = sum ca[k] t^k/k!, degree 3
+    h = 0.125
+    a0, j0 = (_poly(ca, 0.0, k) for k in range(2))
+    a1, j1 = (_poly(ca, h, k) for k in range(2))
+    s1, c1 = oracle.interp4(h, a0, j0, a1, j1)
+    assert rel(s1, _poly(ca, h, 2)) < 1e-11
+    assert rel(c1, _poly(ca, h, 3)) < 1e-10
+
+
+def test_kepler_integration_fourth_order():
+    """The p = 4 scheme converges at 4th order on the Kepler orbit (error ratio
+    2^4 = 16 per halving of eta) and follows the closed form."""
+    mp.mp.dps = 30
+    p = inputs.kepler_pair()
+    T = 8.0
+    ref = np.array([float(x) for x in _kepler(mp.mpf(T))])
+    errs = []
+    for eta in (0.04, 0.02, 0.01):
+        s = oracle.System(p.mass, p.pos, p.vel, 0.0, eta, eta_init=eta / 45, dt_max=1.0, order=4)
+        s.advance(T)
+        x = s.get("pos")
+        errs.append(np.linalg.norm((x[1] - x[0]) - ref))
+        assert np.all(s.get("snap") == 0) and np.all(s.get("crackle") == 0)
+    assert errs[-1] < 1e-7
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 10.0 < e1 / e2 < 25.0, errs      # 2^4 = 16
+
+
+def test_energy_conservation_plummer_1024_fourth_order():
+    p = inputs.plummer(1024, 1)
+    s = oracle.System(p.mass, p.pos, p.vel, 1e-3, 0.15, 0.01, 2.0 ** -25, 1.0 / 16, order=4)
+    E0 = sum(s.energy())
+    s.advance(0.125)
+    assert np.all(s.get("t") == 0.125)
+    assert abs((sum(s.energy()) - E0) / E0) < 3e-8
+
+
 # --------------------------------------------------------------------------
 # Time steps and block selection (hand-computed golden cases).
 # --------------------------------------------------------------------------

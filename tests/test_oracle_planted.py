@@ -27,6 +27,8 @@ PLANTED = [
     ("predictor crackle term h^5/24", "c[q] * h5 / 120.0;", "c[q] * h5 / 24.0;"),
     ("potential counted half", "W -= mass[i] * mass[j]", "W -= 0.5 * mass[i] * mass[j]"),
     ("criterion exponent 1/2 for p = 6", "return eta * cbrt(ratio);", "return eta * sqrt(ratio);"),
+    ("4th-order corrector h^2/12 read as h^2/10", "+ h * h / 12.0 * (j0[k] - j1[k]);", "+ h * h / 10.0 * (j0[k] - j1[k]);"),
+    ("4th-order interpolation: crackle coefficient", "double c = (12.0 * (a0[k] - a1[k])", "double c = (10.0 * (a0[k] - a1[k])"),
     ("angular momentum component sign", "Lz += mass[i] * (r[0] * u[1] - r[1] * u[0]);",
      "Lz += mass[i] * (r[1] * u[0] - r[0] * u[1]);"),
 ]
