@@ -71,6 +71,8 @@ def parse():
                     help="independent-clusters workload: batched context vs one context per cluster")
     ap.add_argument("--clusters", type=int, default=512)
     ap.add_argument("--t-end", type=float, default=0.125, help="block-sizes mode: integrate from 0 to this time")
+    ap.add_argument("--order", type=int, choices=[4, 6], default=6,
+                    help="integration order: 6 (the paper's scheme) or 4 (p = 4 criterion)")
     ap.add_argument("--precisions", default="fp64,mixed", help="block-sizes / eta-sweep modes: which paths")
     ap.add_argument("--mode", choices=["interval", "batch", "block-sizes", "accuracy", "large", "eta-sweep"],
                     default="interval",
@@ -630,16 +632,16 @@ def run_eta_sweep(a):
     n = a.n
     p = inputs.plummer(n, a.seed, imf=a.imf)
     T = a.t_end
-    etas = (0.15, 0.3, 0.45, 0.6, 0.8, 1.0)
+    etas = (0.15, 0.3, 0.45, 0.6, 0.8, 1.0) if a.order == 6 else (0.05, 0.1, 0.15, 0.2, 0.3)
     wanted = {"fp64": hg.HG_FP64, "mixed": hg.HG_MIXED}
-    out = {"metric": "energy and angular-momentum errors against eta (Sect. 5.1)",
+    out = {"metric": "energy and angular-momentum errors against eta (Sect. 5.1)", "order": a.order,
            "config": {"workload": f"Plummer N={n}, {a.imf} masses (seed {a.seed}), eps={a.eps:g}, dt_max=1/16, "
                                   f"t = 0 -> {T:g}, errors at t_i = i {T / 10:g}, i = 1..10; FP64 energy sums"}}
     for name in [x for x in a.precisions.split(",") if x]:
         rows = []
         for eta in etas:
             o = hg.hg_default_opts(precision=wanted[name], energy_precision=hg.HG_FP64, dt_max=1.0 / 16,
-                                   stream=stream)
+                                   stream=stream, order=a.order)
             ctx = hg.hg_init(p.mass, p.pos, p.vel, a.eps, eta, o)
             E0 = sum(hg.hg_energy(ctx))
             L0 = float(np.linalg.norm(hg.hg_angular_momentum(ctx)))

@@ -57,7 +57,10 @@ typedef struct hg_opts {
     int32_t test_stall_eval;  /* testing only: 1 = every evaluation expects bytes that are never
                                  copied, so its bounded waits run out (~2 s) and the call returns
                                  HG_ETIMEOUT; exercises the failure path without a fault */
-    int32_t reserved;
+    int32_t order;            /* integration order: 6 (default; 0 also means 6) is the paper's 6th-order
+                                 Hermite scheme; 4 is the 4th-order Hermite scheme its step criterion
+                                 admits with p = 4 (corrector from a and jerk, snap and crackle from the
+                                 cubic interpolant; stored snap and crackle stay zero) */
     double dt_min;            /* smallest step, power of two (default 2^-25, Sect. 3) */
     double dt_max;            /* largest step, power of two (default 2^-3, Sect. 3) */
     double eta_init;          /* accuracy parameter of the first step (p = 4 criterion; default 0.01) */

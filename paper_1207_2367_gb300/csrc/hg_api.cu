@@ -126,6 +126,7 @@ StepParams step_params(const hg_ctx *c)
     // below 3e-6 |a| carries no usable higher-derivative information.
     p.noise_rel = c->mixed ? 3e-6 : 0.0;
     p.log2_eta = (float)log2(c->eta);
+    p.order = c->opts.order;
     return p;
 }
 
@@ -665,7 +666,7 @@ void hg_default_opts(hg_opts *o)
     o->start_mode = 0;
     o->profile = 0;
     o->test_stall_eval = 0;
-    o->reserved = 0;
+    o->order = 6;
     o->dt_min = 1.0 / 33554432.0;   // 2^-25
     o->dt_max = 0.125;              // 2^-3
     o->eta_init = 0.01;
@@ -723,6 +724,8 @@ int hg_init_batch(hg_ctx **out, int32_t n_clusters, const int64_t *offsets, int6
     if (o.graph_steps < 1 || o.graph_steps > 1024) return bad("graph_steps must be in [1, 1024]");
     if (o.start_mode != 0 && o.start_mode != 1) return bad("start_mode must be 0 or 1");
     if (o.test_stall_eval != 0 && o.test_stall_eval != 1) return bad("test_stall_eval must be 0 or 1");
+    if (o.order == 0) o.order = 6;
+    if (o.order != 4 && o.order != 6) return bad("order must be 4 or 6");
 
     hg_ctx *c = new (std::nothrow) hg_ctx();
     if (!c) {

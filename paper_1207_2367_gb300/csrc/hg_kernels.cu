@@ -521,7 +521,7 @@ __global__ void k_start(State st, int64_t n, const double *ra, const double *rj,
             d[3][k] = 0.0;
             st.a[3 * i + k] = d[0][k];
             st.j[3 * i + k] = d[1][k];
-            st.s[3 * i + k] = d[2][k];
+            st.s[3 * i + k] = sp.order == 4 ? 0.0 : d[2][k];   // the 4th-order scheme keeps a, jerk
             st.c[3 * i + k] = 0.0;
         }
         st.t[i] = 0.0;
@@ -600,7 +600,44 @@ __device__ __forceinline__ void correct_component(const State &st, int64_t i, in
     st.c[q] = c3;
 }
 
-// ---- FP32 estimate of floor(log2 crit) for the p = 6 criterion -------------
+// 4th-order scheme, component k of particle i (the two-point Hermite corrector
+// and the cubic interpolant through a and jerk at both ends): corrected v and r,
+// new a and jerk (snap and crackle stored as zero: the predictor ends at jerk),
+// and snap and crackle at the step's end for the p = 4 criterion.  h = 2^e:
+// h^2/12 = 2^(2e) fl(1/12) and the reciprocal powers are exact scalings.
+__device__ __forceinline__ void correct4_component(const State &st, int64_t i, int k, double h, int e, bool pow2,
+                                                   double a1, double j1, double &s1, double &c1, double &Ak)
+{
+    double hh, h2, ih2, ih3;
+    if (pow2) {
+        hh = pow2i(e - 1);
+        h2 = pow2i(2 * e) * (1.0 / 12.0);
+        ih2 = pow2i(-2 * e);
+        ih3 = pow2i(-3 * e);
+    } else {
+        hh = h / 2.0;
+        h2 = h * h / 12.0;
+        ih2 = 1.0 / (h * h);
+        ih3 = ih2 / h;
+    }
+    const int64_t q = 3 * i + k;
+    const double x0 = st.x[q], v0 = st.v[q], a0 = st.a[q], j0 = st.j[q];
+    const double v1 = v0 + hh * (a0 + a1) + h2 * (j0 - j1);
+    const double x1 = x0 + hh * (v0 + v1) + h2 * (a0 - a1);
+    const double c = (12.0 * (a0 - a1) + 6.0 * h * (j0 + j1)) * ih3;
+    const double s0 = (-6.0 * (a0 - a1) - h * (4.0 * j0 + 2.0 * j1)) * ih2;
+    s1 = s0 + c * h;
+    c1 = c;
+    Ak = a1 - a0 - j0 * h;
+    st.x[q] = x1;
+    st.v[q] = v1;
+    st.a[q] = a1;
+    st.j[q] = j1;
+    st.s[q] = 0.0;
+    st.c[q] = 0.0;
+}
+
+// ---- FP32 estimate of floor(log2 crit) for the step criterion --------------
 // Logarithms are carried as e + r: an exact integer e and a small float r, so
 // that exponents up to +-2046 keep ~1e-7 absolute precision.  Every step below
 // (mantissa truncated to 24 bits, lg2/ex2 approximations) errs by < 1e-6 in
@@ -646,20 +683,22 @@ __device__ __forceinline__ Log2 l2_sum(Log2 a, Log2 b)
     return Log2{a.e, a.r + __log2f(1.0f + exp2f(-d))};
 }
 
-// floor(log2(eta (A1 / A4)^(1/3))) with A1 = sqrt(n0 n2 + n1^2), A4 = sqrt(n3 n5 + n4^2),
-// n_s = |d_s|, from the squared norms q_s; false when undecided (a q_s that is
-// zero or not normal, or the estimate within kLogGuard of an integer).
-__device__ __forceinline__ bool criterion6_floor_log2(const double *qn, float log2_eta, int &F)
+// floor(log2(eta (A1 / A_{p-2})^(1/(p-3)))) for p = 4 or 6, with A1 = sqrt(n0 n2 +
+// n1^2), A_{p-2} = sqrt(n_{p-3} n_{p-1} + n_{p-2}^2), n_s = |d_s|, from the
+// squared norms q_s; false when undecided (a q_s that is zero or not normal, or
+// the estimate within kLogGuard of an integer).
+template <int P>
+__device__ __forceinline__ bool criterion_floor_log2(const double *qn, float log2_eta, int &F)
 {
-    Log2 l[6];
+    Log2 l[P];
 #pragma unroll
-    for (int s = 0; s < 6; ++s)
+    for (int s = 0; s < P; ++s)
         if (!log2_of(qn[s], l[s])) return false;
     // log2 A^2 terms: log2(n0 n2) = (L0 + L2) / 2, log2(n1^2) = L1 (L = log2 q).
     const Log2 A1sq = l2_sum(l2_div(l2_add(l[0], l[2]), 2), l[1]);
-    const Log2 A4sq = l2_sum(l2_div(l2_add(l[3], l[5]), 2), l[4]);
-    // log2 crit = log2 eta + (log2 A1^2 - log2 A4^2) / 6
-    const Log2 x = l2_div(Log2{A1sq.e - A4sq.e, A1sq.r - A4sq.r}, 6);
+    const Log2 Apsq = l2_sum(l2_div(l2_add(l[P - 3], l[P - 1]), 2), l[P - 2]);
+    // log2 crit = log2 eta + (log2 A1^2 - log2 A_{p-2}^2) / (2 (p - 3))
+    const Log2 x = l2_div(Log2{A1sq.e - Apsq.e, A1sq.r - Apsq.r}, 2 * (P - 3));
     const float y = log2_eta + x.r;
     const float fy = floorf(y);
     const float frac = y - fy;
@@ -686,6 +725,7 @@ __device__ __forceinline__ double sq3(const double *p) { return p[0] * p[0] + p[
 // A: the acceleration change left after a0 + j0 h + s0 h^2/2.  Below the noise
 // floor of the evaluation (sp.noise_rel |a1|, compared as squares) the
 // interpolated derivatives are noise and the criterion may not shrink the step.
+template <int P>
 __device__ __forceinline__ double finish_step(const State &st, int64_t i, double h, int e, bool pow2,
                                               const double (*d)[3], const double *A, const StepParams &sp)
 {
@@ -693,11 +733,11 @@ __device__ __forceinline__ double finish_step(const State &st, int64_t i, double
     const bool noisy = sp.noise_rel > 0.0 && sq3(A) < (sp.noise_rel * sp.noise_rel) * sq3(d[0]);
     double dt1;
     int F, kmin, kmax;
-    double qn[6];
+    double qn[P];
 #pragma unroll
-    for (int s = 0; s < 6; ++s) qn[s] = sq3(d[s]);
+    for (int s = 0; s < P; ++s) qn[s] = sq3(d[s]);
     if (pow2 && pow2_exponent(sp.dt_min, kmin) && pow2_exponent(sp.dt_max, kmax) &&
-        (noisy || criterion6_floor_log2(qn, sp.log2_eta, F))) {
+        (noisy || criterion_floor_log2<P>(qn, sp.log2_eta, F))) {
         // The power-of-two rule (block_dt) on exponents: shrink to max(F, k_min)
         // when crit < h, double when crit >= 2h, 2h <= dt_max and t1 is a
         // multiple of 2h; clamp to [dt_min, dt_max].
@@ -710,7 +750,7 @@ __device__ __forceinline__ double finish_step(const State &st, int64_t i, double
         kn = kn < kmin ? kmin : (kn > kmax ? kmax : kn);
         dt1 = pow2i(kn);
     } else {
-        double crit = criterion(sp.eta, 6, d);
+        double crit = criterion(sp.eta, P, d);
         if (noisy) crit = INFINITY;
         dt1 = block_dt(crit, h, t1, sp.dt_min, sp.dt_max);
     }
@@ -734,6 +774,16 @@ __global__ void __launch_bounds__(128) k_correct(State st, const int32_t *idx, c
         int e = 0;
         const bool pow2 = pow2_exponent(h, e);
         double d[6][3], A[3];
+        if (sp.order == 4) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                d[0][k] = ra[3 * q + k];
+                d[1][k] = rj[3 * q + k];
+                correct4_component(st, i, k, h, e, pow2, d[0][k], d[1][k], d[2][k], d[3][k], A[k]);
+            }
+            low = min(low, __double_as_longlong(finish_step<4>(st, i, h, e, pow2, d, A, sp)));
+            continue;
+        }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             double c3, c4, c5;
@@ -745,7 +795,7 @@ __global__ void __launch_bounds__(128) k_correct(State st, const int32_t *idx, c
             d[4][k] = c4;
             d[5][k] = c5;
         }
-        low = min(low, __double_as_longlong(finish_step(st, i, h, e, pow2, d, A, sp)));
+        low = min(low, __double_as_longlong(finish_step<6>(st, i, h, e, pow2, d, A, sp)));
     }
     if (!min_pass) return;
     // Next block time: min over the new tend of the particles corrected here and

@@ -11,7 +11,8 @@ struct StepParams {
     // When |a1 - a0 - j0 h - s0 h^2/2| < noise_rel |a1| the interpolated crackle,
     // pop and 5th derivative are unresolved: the criterion then does not shrink the step.
     double noise_rel;
-    float log2_eta;   // log2(eta), for the FP32 estimate of the p = 6 criterion
+    float log2_eta;   // log2(eta), for the FP32 estimate of the criterion
+    int order;        // 6: the paper's scheme (p = 6); 4: the 4th-order scheme (p = 4)
 };
 
 constexpr int64_t kNBChunk = 2048;   // particles per CTA in the next-block passes

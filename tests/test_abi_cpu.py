@@ -33,5 +33,5 @@ def test_default_opts_without_gpu():
     o = binding.hg_default_opts()
     assert o.dt_min == 2.0 ** -25 and o.dt_max == 0.125 and o.eta_init == 0.01
     assert o.precision == binding.HG_FP64 and o.graph_steps == 8 and o.start_mode == 0 and o.profile == 0
-    assert o.test_stall_eval == 0
+    assert o.test_stall_eval == 0 and o.order == 6
     assert ctypes.sizeof(binding.hg_opts) == 10 * 4 + 3 * 8 + 8
