@@ -42,9 +42,12 @@ def test_order4_block_steps_with_injection_match_oracle(hg, precision):
             got, t_sys = gpu_state(hg, ctx, n)
             assert t_sys == tn
             ids = idx_ref
-            for f, tol in (("pos", 1e-13 if precision == 0 else 1e-9), ("vel", 1e-12 if precision == 0 else 1e-7),
-                           ("acc", TOL[precision][0]), ("jerk", TOL[precision][1])):
+            for f, tol in (("pos", 1e-13 if precision == 0 else 1e-9), ("vel", 1e-12 if precision == 0 else 1e-7)):
                 assert rel_rows(got[f][ids], sysm.get(f)[ids]).max() < tol, f
+            for f, tol in (("acc", TOL[precision][0]), ("jerk", TOL[precision][1])):
+                g, r = got[f][ids], sysm.get(f)[ids]
+                err = rel_rows(g, r).max() if precision == 0 else np.linalg.norm(g - r) / np.linalg.norm(r)
+                assert err < tol, (f, err)   # mixed: normwise, as for the evaluation itself
             assert np.all(got["snap"][ids] == 0) and np.all(got["crackle"][ids] == 0)
             np.testing.assert_array_equal(got["t"], sysm.get("t"))
             dt_mismatch += int(np.sum(got["dt"][ids] != sysm.get("dt")[ids]))
