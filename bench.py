@@ -71,6 +71,8 @@ def parse():
                     help="independent-clusters workload: batched context vs one context per cluster")
     ap.add_argument("--clusters", type=int, default=512)
     ap.add_argument("--t-end", type=float, default=0.125, help="block-sizes mode: integrate from 0 to this time")
+    ap.add_argument("--bh-mass", type=float, default=0.0,
+                    help="block-sizes mode: add a central object of this mass (stars: total mass 1)")
     ap.add_argument("--order", type=int, choices=[4, 6], default=6,
                     help="integration order: 6 (the paper's scheme) or 4 (p = 4 criterion)")
     ap.add_argument("--precisions", default="fp64,mixed", help="block-sizes / eta-sweep modes: which paths")
@@ -544,9 +546,13 @@ def run_block_sizes(a):
     hg.load()
     stream = torch.cuda.Stream()
     mhz, kind = sm_max_mhz()
-    p = inputs.plummer(a.n, a.seed, imf=a.imf)
+    if a.bh_mass > 0:
+        p = inputs.plummer_black_hole(a.n, a.seed, a.bh_mass, imf=a.imf)
+    else:
+        p = inputs.plummer(a.n, a.seed, imf=a.imf)
+    bh = f" + central object of mass {a.bh_mass:g} (particle N-1)" if a.bh_mass > 0 else ""
     out = {"metric": "evaluation time per block-size bucket", "unit": "us",
-           "config": {"workload": f"Plummer N={a.n}, {a.imf} masses (seed {a.seed}), eps={a.eps:g}, eta=0.45, "
+           "config": {"workload": f"Plummer N={a.n}, {a.imf} masses (seed {a.seed}){bh}, eps={a.eps:g}, eta=0.45, "
                                   f"dt_max=1/16, t = 0 -> {a.t_end:g}, every block step"}}
     wanted = {"fp64": hg.HG_FP64, "mixed": hg.HG_MIXED}
     for name in [x for x in a.precisions.split(",") if x]:

@@ -147,6 +147,24 @@ def plummer(n: int, seed: int, imf: str = "equal", henon: bool = True) -> Partic
     return ParticleSet(mass=mass, pos=np.ascontiguousarray(pos), vel=np.ascontiguousarray(vel))
 
 
+def plummer_black_hole(n: int, seed: int, m_bh: float = 0.01, imf: str = "equal") -> ParticleSet:
+    """A Plummer sphere of n - 1 stars (total mass 1, Henon units) with a massive
+    central object of mass m_bh, at rest at the origin before the whole set is
+    moved to its centre-of-mass frame.  The black hole is the last particle.
+    The stars are not re-equilibrated: a workload with a deep central potential
+    (the massive-object case of Sect. 5.5), not an equilibrium model."""
+    if n < 2 or not m_bh > 0.0:
+        raise ValueError("need n >= 2 and m_bh > 0")
+    stars = plummer(n - 1, seed, imf)
+    mass = np.concatenate([stars.mass, [m_bh]])
+    pos = np.concatenate([stars.pos, np.zeros((1, 3))])
+    vel = np.concatenate([stars.vel, np.zeros((1, 3))])
+    mt = mass.sum()
+    pos -= (mass[:, None] * pos).sum(0) / mt
+    vel -= (mass[:, None] * vel).sum(0) / mt
+    return ParticleSet(mass=mass, pos=np.ascontiguousarray(pos), vel=np.ascontiguousarray(vel))
+
+
 def cluster_sizes(n_clusters: int, seed: int, n_lo: int = 256, n_hi: int = 16384) -> np.ndarray:
     """Cluster sizes log-uniform in [n_lo, n_hi]: round(exp(U[ln n_lo, ln n_hi]))."""
     u = uniform(seed, np.arange(n_clusters), 0)

@@ -259,6 +259,43 @@ def test_energy_matches_oracle(hg):
             hg.hg_free(ctx)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_black_hole_system_matches_oracle(hg, precision):
+    """A Plummer sphere with a central object of 5 % of its mass (the
+    massive-object case of Sect. 5.5): evaluations of all particles and of
+    random subsets, and 20 injected block steps with their new steps."""
+    n, eps = 1024, 1e-4
+    p = inputs.plummer_black_hole(n, 11, m_bh=0.05)
+    sysm = oracle.System(p.mass, p.pos, p.vel, eps, 0.45, 0.01, DT_MIN, DT_MAX)
+    for _ in range(3):
+        sysm.step()
+    ctx = gpu_context(hg, sysm, precision, eps)
+    dt_mismatch = active = 0
+    try:
+        t = sysm.t_sys + 2.0 ** -12
+        rng = np.random.default_rng(4)
+        for idx in (np.arange(n), np.array([n - 1]), np.sort(rng.choice(n, 100, replace=False))):
+            check_eval(gpu_eval(hg, ctx, idx, t), sysm.predict_eval(t, idx), precision, sysm.predict_absum(t, idx))
+        for _ in range(20):
+            st = sysm.get_state()
+            hg.hg_set_state(ctx, {f: st[f] for f in hg.STATE_FIELDS}, st["t_sys"])
+            tn, m = hg.hg_next_block(ctx)
+            hg.hg_predict(ctx, tn)
+            hg.hg_evaluate(ctx, None, m)
+            hg.hg_correct(ctx, None, m)
+            sysm.step()
+            got, t_sys = gpu_state(hg, ctx, n)
+            assert t_sys == sysm.t_sys
+            np.testing.assert_array_equal(got["t"], sysm.get("t"))
+            ids = np.nonzero(got["t"] == t_sys)[0]
+            dt_mismatch += int(np.sum(got["dt"][ids] != sysm.get("dt")[ids]))
+            active += len(ids)
+            assert rel_rows(got["pos"], sysm.get("pos")).max() < (1e-13 if precision == 0 else 1e-9)
+        assert dt_mismatch <= (0 if precision == 0 else max(1, active // 200)), (dt_mismatch, active)
+    finally:
+        hg.hg_free(ctx)
+
+
 def test_angular_momentum_matches_oracle(hg):
     """L of the predicted system at the last block time (oracle state injected;
     particles at their own times), against the oracle's sum, relative to the

@@ -59,3 +59,15 @@ def test_cluster_batch_sizes():
     sizes = inputs.cluster_sizes(512, 4)
     assert sizes.min() >= 256 and sizes.max() <= 16384
     assert 2500 < sizes.mean() < 5500
+
+
+def test_plummer_black_hole():
+    p = inputs.plummer_black_hole(1001, 3, m_bh=0.02)
+    assert p.mass.shape == (1001,) and p.mass[-1] == 0.02
+    assert abs(p.mass[:-1].sum() - 1.0) < 1e-14
+    mt = p.mass.sum()
+    assert np.abs((p.mass[:, None] * p.pos).sum(0) / mt).max() < 1e-15
+    assert np.abs((p.mass[:, None] * p.vel).sum(0) / mt).max() < 1e-15
+    # the stars are the plain Plummer sphere of n - 1, shifted by the centre of mass
+    s = inputs.plummer(1000, 3)
+    np.testing.assert_allclose(p.pos[:-1] - p.pos[-1], s.pos, atol=1e-15)
