@@ -845,7 +845,8 @@ int hg_correct(hg_ctx *c, const int32_t *idx, int64_t m)
     if (rc) return rc;
     if (flag)
         return fail(c, HG_ESTATE, "list differs from the evaluation, or a particle is not due at the block time");
-    const int cgrid = (int)std::min<int64_t>((m + 127) / 128, 2 * (int64_t)c->num_sms);
+    // 3 lanes per particle, units of 10 particles per warp, 4 warps per CTA
+    const int cgrid = (int)std::min<int64_t>(((m + 9) / 10 + 3) / 4, 2 * (int64_t)c->num_sms);
     HG_CUDA(c, launch_correct(c->st, c->d_idx, nullptr, m, c->n, c->ra, c->rj, c->rs, step_params(c), c->d_sc, 0,
                               cgrid, c->stream));
     c->tnext_valid = false;

@@ -112,6 +112,18 @@ __host__ __device__ inline int64_t plan_tps(int k)
     return t[k];
 }
 
+// ceil(a / b) for a >= 0, b > 0; 32-bit division when both fit (a 64-bit
+// division is a long software sequence on the GPU and the device planner scores
+// hundreds of candidates per block step).  Exact either way.
+__host__ __device__ inline int64_t div_ceil(int64_t a, int64_t b)
+{
+    if (((uint64_t)a | (uint64_t)b) < 0x80000000ull) {
+        const uint32_t a32 = (uint32_t)a, b32 = (uint32_t)b;
+        return (int64_t)((a32 + b32 - 1u) / b32);
+    }
+    return (a + b - 1) / b;
+}
+
 // Fill p for candidate c and return its modelled cost (-1: not admissible).
 // cost = waves * (tiles per item * (TJ / tpi + c_tile) + c_item), integers only
 // so that host and device choose the same plan.
@@ -127,20 +139,20 @@ __host__ __device__ inline int64_t plan_candidate(int64_t m, const PlanParams &q
     if (q.b_force > 0) {
         if (c % 32 != 0) return -1;
         const int64_t b = q.b_force < q.ntiles ? q.b_force : q.ntiles;
-        tps = (q.ntiles + b - 1) / b;
+        tps = div_ceil(q.ntiles, b);
     }
     if (tps > q.ntiles) return -1;
-    const int64_t b = (q.ntiles + tps - 1) / tps;
+    const int64_t b = div_ceil(q.ntiles, tps);
     const int64_t mm = m > 0 ? m : 1;
     if (b * mm > q.pcap && b > 1) return -1;
     p.tpi = tpi;
     p.ti = kEvalThreads / tpi * ipt;
-    p.n_itiles = (mm + p.ti - 1) / p.ti;
+    p.n_itiles = div_ceil(mm, p.ti);
     p.tiles_per_split = tps;
     p.b = (int)b;
     p.variant = v;
     p.n_items = p.n_itiles * b;
-    const int64_t waves = (p.n_items + grid - 1) / grid;
+    const int64_t waves = div_ceil(p.n_items, grid);
     const int64_t w = v == 0 ? 100 : (waves > 1 ? q.weight1 : q.weight1_one);
     return waves * (tps * ((q.tj / tpi) * w + q.c_tile * 100) + q.c_item * 100);
 }

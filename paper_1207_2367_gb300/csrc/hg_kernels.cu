@@ -727,7 +727,8 @@ __device__ __forceinline__ double sq3(const double *p) { return p[0] * p[0] + p[
 // interpolated derivatives are noise and the criterion may not shrink the step.
 template <int P>
 __device__ __forceinline__ double finish_step(const State &st, int64_t i, double h, int e, bool pow2,
-                                              const double (*d)[3], const double *A, const StepParams &sp)
+                                              const double (*d)[3], const double *A, const StepParams &sp,
+                                              bool store)
 {
     const double t1 = st.t[i] + h;
     const bool noisy = sp.noise_rel > 0.0 && sq3(A) < (sp.noise_rel * sp.noise_rel) * sq3(d[0]);
@@ -754,10 +755,57 @@ __device__ __forceinline__ double finish_step(const State &st, int64_t i, double
         if (noisy) crit = INFINITY;
         dt1 = block_dt(crit, h, t1, sp.dt_min, sp.dt_max);
     }
-    st.t[i] = t1;
-    st.dt[i] = dt1;
-    st.tend[i] = t1 + dt1;
+    if (store) {
+        st.t[i] = t1;
+        st.dt[i] = dt1;
+        st.tend[i] = t1 + dt1;
+    }
     return t1 + dt1;
+}
+
+// Three lanes per particle, one per component: warp w takes units of 10
+// particles (lanes 3p, 3p+1, 3p+2 hold particle p of the unit; lanes 30 and 31
+// idle).  Each lane corrects its component; shuffles then give every lane of the
+// triple all components, and the three run the same step logic on the same
+// values (the first stores the new time and step).  The chain of dependent FP64
+// instructions of a small block is a third of the one-thread-per-particle form.
+constexpr int kCorrUnit = 10;
+
+template <int P>
+__device__ __forceinline__ void correct_lane(const State &st, const int32_t *idx, const double *ra, const double *rj,
+                                             const double *rs, const StepParams &sp, int64_t m, int64_t u,
+                                             long long &low)
+{
+    const int lane = threadIdx.x & 31, sub = lane / 3, k = lane - 3 * sub;
+    const int64_t q = u * kCorrUnit + sub;
+    const bool act = sub < kCorrUnit && q < m;
+    double dk[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, Ak = 0.0, h = 1.0;
+    int64_t i = 0;
+    int e = 0;
+    bool pow2 = false;
+    if (act) {
+        i = idx[q];
+        h = st.dt[i];
+        pow2 = pow2_exponent(h, e);
+        dk[0] = ra[3 * q + k];
+        dk[1] = rj[3 * q + k];
+        if (P == 4) {
+            correct4_component(st, i, k, h, e, pow2, dk[0], dk[1], dk[2], dk[3], Ak);
+        } else {
+            dk[2] = rs[3 * q + k];
+            correct_component(st, i, k, h, e, pow2, dk[0], dk[1], dk[2], dk[3], dk[4], dk[5], Ak);
+        }
+    }
+    double d[6][3], A[3];
+    const int base = 3 * sub;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int src = base + c < 32 ? base + c : 31;
+#pragma unroll
+        for (int r = 0; r < P; ++r) d[r][c] = __shfl_sync(0xffffffffu, dk[r], src);
+        A[c] = __shfl_sync(0xffffffffu, Ak, src);
+    }
+    if (act) low = min(low, __double_as_longlong(finish_step<P>(st, i, h, e, pow2, d, A, sp, k == 0)));
 }
 
 __global__ void __launch_bounds__(128) k_correct(State st, const int32_t *idx, const int64_t *m_dev, int64_t m_host,
@@ -768,34 +816,13 @@ __global__ void __launch_bounds__(128) k_correct(State st, const int32_t *idx, c
     const int64_t m = m_dev ? *m_dev : m_host;
     if (m <= 0) return;
     long long low = LLONG_MAX;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = idx[q];
-        const double h = st.dt[i];
-        int e = 0;
-        const bool pow2 = pow2_exponent(h, e);
-        double d[6][3], A[3];
-        if (sp.order == 4) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                d[0][k] = ra[3 * q + k];
-                d[1][k] = rj[3 * q + k];
-                correct4_component(st, i, k, h, e, pow2, d[0][k], d[1][k], d[2][k], d[3][k], A[k]);
-            }
-            low = min(low, __double_as_longlong(finish_step<4>(st, i, h, e, pow2, d, A, sp)));
-            continue;
-        }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            double c3, c4, c5;
-            correct_component(st, i, k, h, e, pow2, ra[3 * q + k], rj[3 * q + k], rs[3 * q + k], c3, c4, c5, A[k]);
-            d[0][k] = ra[3 * q + k];
-            d[1][k] = rj[3 * q + k];
-            d[2][k] = rs[3 * q + k];
-            d[3][k] = c3;
-            d[4][k] = c4;
-            d[5][k] = c5;
-        }
-        low = min(low, __double_as_longlong(finish_step<6>(st, i, h, e, pow2, d, A, sp)));
+    const int64_t units = (m + kCorrUnit - 1) / kCorrUnit;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units; u += nw) {   // warp-uniform
+        if (sp.order == 4)
+            correct_lane<4>(st, idx, ra, rj, rs, sp, m, u, low);
+        else
+            correct_lane<6>(st, idx, ra, rj, rs, sp, m, u, low);
     }
     if (!min_pass) return;
     // Next block time: min over the new tend of the particles corrected here and
