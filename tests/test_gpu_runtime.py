@@ -1,5 +1,5 @@
 """GPU runtime behaviour: checkpoint/resume, the bounded-wait failure path, and
-parity at the full sizes of the N = 65536 and N = 2^20 configurations on
+parity at the full sizes of the N = 65536, 2^20 and 2^23 configurations on
 sampled outputs (the oracle evaluates the sampled particles one by one)."""
 import time
 
@@ -74,6 +74,40 @@ def test_full_size_n65536_fp64_sampled(hg):
     ref = oracle.evaluate(p.mass, p.pos, p.vel, np.zeros((n, 3)), eps, idx)
     for f, r in zip(("acc", "jerk", "snap"), ref):
         assert rel_rows(st[f][idx], r).max() <= 1e-12, f
+
+
+def test_full_size_n8388608_mixed_sampled(hg):
+    """Configuration N = 2^23 (Salpeter masses, seed 5, eps = 1e-4) on the
+    mixed path, the largest context the benchmark builds: 24 sampled particles
+    evaluated against all 8.4M predicted particles, once as a block of 24
+    (small-block kernel, j split over every SM) and once inside a block of 65536
+    (large-block kernel), against the oracle's sums (normwise and
+    condition-scaled).  The state is given without the start-up (zero
+    derivatives, t = 0), so the prediction is the identity and the oracle needs
+    only positions and velocities."""
+    n, eps = 1 << 23, 1e-4
+    p = inputs.plummer(n, 5, imf="salpeter")
+    rng = np.random.default_rng(5)
+    idx = np.sort(rng.choice(n, 24, replace=False)).astype(np.int32)
+    big = np.union1d(idx, rng.choice(n, 65536 - 24, replace=False)).astype(np.int32)
+    pos_in_big = np.searchsorted(big, idx)
+    ctx = hg.hg_init(p.mass, p.pos, p.vel, eps, 0.45,
+                     hg.hg_default_opts(precision=hg.HG_MIXED, dt_max=DT_MAX, start_mode=1))
+    try:
+        hg.hg_predict(ctx, 0.0)
+        small = [np.empty((24, 3)) for _ in range(3)]
+        hg.hg_evaluate(ctx, idx, 24, *small)
+        large = [np.empty((len(big), 3)) for _ in range(3)]
+        hg.hg_evaluate(ctx, big, len(big), *large)
+    finally:
+        hg.hg_free(ctx)
+    z = np.zeros((n, 3))
+    ref = oracle.evaluate(p.mass, p.pos, p.vel, z, eps, idx)
+    scale = oracle.eval_absum(p.mass, p.pos, p.vel, z, eps, idx)
+    for res in (small, [x[pos_in_big] for x in large]):
+        for k, (f, g, r, tol) in enumerate(zip(("acc", "jerk", "snap"), res, ref, (1e-6, 1e-5, 1e-4))):
+            assert np.linalg.norm(g - r) / np.linalg.norm(r) <= tol, f
+            assert (np.linalg.norm(g - r, axis=1) / scale[:, k]).max() <= tol, f
 
 
 def test_full_size_n1048576_mixed(hg):
