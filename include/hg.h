@@ -181,6 +181,19 @@ int hg_angular_momentum(hg_ctx *ctx, double *L);
 int hg_get_state(hg_ctx *ctx, hg_state *out);
 int hg_set_state(hg_ctx *ctx, const hg_state *in);
 
+/* Bind caller-owned device arrays (e.g. torch tensors) as the context's state:
+ * dev's nine arrays (n or [n][3] doubles each, device memory of the context's
+ * GPU, 8-byte aligned; t_sys is ignored) replace the context's own, so the
+ * caller reads and writes the state in place.  copy_in != 0 first copies the
+ * current state into them; copy_in = 0 takes what they hold, which must pass the
+ * checks of hg_set_state (HG_EINVAL otherwise, nothing bound).  dev = NULL
+ * unbinds: the state is copied back into the context's own arrays.  The caller
+ * keeps the arrays alive while bound (hg_free never frees them) and touches
+ * them only when the context's stream is idle (after a synchronizing call, or
+ * ordered on that stream).  The captured graphs are rebuilt on their next use.
+ * (The binding is a library convenience; the paper has no counterpart.) */
+int hg_bind_device(hg_ctx *ctx, const hg_state *dev, int copy_in);
+
 /* Device counters (synchronizes). */
 int hg_get_stats(hg_ctx *ctx, hg_stats *out);
 

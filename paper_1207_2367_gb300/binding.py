@@ -101,12 +101,13 @@ def load(path: str | None = None):
         L.hg_evaluate_static.argtypes = [I64, P, P, P, P, D, C.c_int32, I32P, I64, P, P, P, P]
         L.hg_evaluate_static.restype = C.c_int
         L.hg_angular_momentum.argtypes = [P, C.POINTER(D)]
+        L.hg_bind_device.argtypes = [P, C.c_void_p, C.c_int]
         L.hg_tune.argtypes = [P, I64, C.c_int32, C.POINTER(hg_tune_entry), C.c_int32, C.POINTER(C.c_int32)]
         L.hg_get_tuning.argtypes = [P, C.POINTER(C.c_int16)]
         L.hg_set_tuning.argtypes = [P, C.POINTER(C.c_int16)]
         for name in ("hg_init", "hg_next_block", "hg_predict", "hg_evaluate", "hg_correct", "hg_step",
                      "hg_advance", "hg_energy", "hg_get_state", "hg_set_state", "hg_get_stats", "hg_get_profile",
-                     "hg_tune", "hg_get_tuning", "hg_set_tuning", "hg_angular_momentum"):
+                     "hg_tune", "hg_get_tuning", "hg_set_tuning", "hg_angular_momentum", "hg_bind_device"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -213,6 +214,16 @@ def hg_angular_momentum(ctx):
     L = (C.c_double * 3)()
     _check(ctx, load().hg_angular_momentum(ctx, L))
     return np.array(list(L))
+
+
+def hg_bind_device(ctx, arrays: dict | None, copy_in: bool = True):
+    """Bind CUDA float64 tensors (keys of STATE_FIELDS) as the context's state;
+    None unbinds.  Keep the tensors alive while bound."""
+    if arrays is None:
+        _check(ctx, load().hg_bind_device(ctx, None, 0))
+        return
+    s = hg_state(**{f: _ptr(arrays[f]) for f in STATE_FIELDS}, t_sys=0.0)
+    _check(ctx, load().hg_bind_device(ctx, C.byref(s), int(bool(copy_in))))
 
 
 def hg_get_state(ctx, out: dict):

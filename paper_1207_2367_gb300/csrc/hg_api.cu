@@ -26,6 +26,8 @@ struct hg_ctx {
     cudaStream_t stream = nullptr, cap_stream = nullptr;
     bool own_stream = false;
     State st{}, st2{};
+    State own{};          // the context's own state arrays (st points at the caller's when bound)
+    bool bound = false;
     Records rec{};
     int32_t *d_idx = nullptr, *d_idx2 = nullptr, *nb_cnt = nullptr, *nb_off = nullptr;
     double *nb_part = nullptr;
@@ -386,6 +388,7 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
         if (c->npad > (int64_t)INT32_MAX) return fail(c, HG_EINVAL, "too many padded records");
     }
     bool ok = alloc_state(c, c->st) && alloc_state(c, c->st2);
+    c->own = c->st;
     if (c->mixed) {
         c->rec.p[0] = dalloc<float4>(c, c->npad);
         c->rec.p[1] = dalloc<float4>(c, c->npad);
@@ -992,6 +995,64 @@ int hg_set_state(hg_ctx *c, const hg_state *in)
     c->tnext_valid = false;
     rc = upload_scalar(c, &c->d_sc->t_cur, in->t_sys);
     if (rc) return rc;
+    invalidate(c);
+    return HG_OK;
+}
+
+int hg_bind_device(hg_ctx *c, const hg_state *dev, int copy_in)
+{
+    if (!c) return HG_EINVAL;
+    const int64_t n = c->n;
+    auto copy_state = [&](const State &dst, const State &src) -> int {
+        struct F {
+            double *d;
+            const double *s;
+            int64_t len;
+        } f[] = {{dst.mass, src.mass, n}, {dst.x, src.x, 3 * n}, {dst.v, src.v, 3 * n}, {dst.a, src.a, 3 * n},
+                 {dst.j, src.j, 3 * n},   {dst.s, src.s, 3 * n}, {dst.c, src.c, 3 * n}, {dst.t, src.t, n},
+                 {dst.dt, src.dt, n}};
+        for (auto &q : f)
+            if (q.d != q.s)
+                HG_CUDA(c, cudaMemcpyAsync(q.d, q.s, q.len * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        return HG_OK;
+    };
+    int rc = HG_OK;
+    if (!dev) {   // unbind: the state goes back into the context's own arrays
+        if (!c->bound) return HG_OK;
+        if ((rc = copy_state(c->own, c->st)) != HG_OK) return rc;
+        c->st = c->own;
+        c->bound = false;
+    } else {
+        double *p[9] = {dev->mass, dev->pos, dev->vel, dev->acc, dev->jerk, dev->snap, dev->crackle, dev->t, dev->dt};
+        for (double *q : p) {
+            cudaPointerAttributes a;
+            if (!q || ((uintptr_t)q & 7u) != 0) return fail(c, HG_EINVAL, "every field must be an 8-byte aligned pointer");
+            if (cudaPointerGetAttributes(&a, q) != cudaSuccess ||
+                (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != c->device) {
+                cudaGetLastError();
+                return fail(c, HG_EINVAL, "every field must be device memory of the context's GPU");
+            }
+        }
+        State b = c->st;
+        b.mass = p[0]; b.x = p[1]; b.v = p[2]; b.a = p[3]; b.j = p[4]; b.s = p[5]; b.c = p[6]; b.t = p[7]; b.dt = p[8];
+        b.tend = c->own.tend;
+        if (copy_in) {
+            if ((rc = copy_state(b, c->st)) != HG_OK) return rc;
+        } else {
+            int32_t flag = 0;
+            rc = device_check(
+                c, [&](int32_t *fl) { return launch_validate_state(b, n, c->opts.dt_min, c->opts.dt_max, fl, c->stream); },
+                &flag);
+            if (rc) return rc;
+            if (flag) return fail(c, HG_EINVAL, "the bound arrays do not hold a valid state");
+        }
+        c->st = b;
+        c->bound = true;
+    }
+    HG_CUDA(c, launch_tend(c->st, n, c->stream));
+    HG_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->tnext_valid = false;
+    drop_graphs(c);   // they captured the old state pointers
     invalidate(c);
     return HG_OK;
 }

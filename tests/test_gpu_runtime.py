@@ -188,3 +188,56 @@ def test_step_choices_equal_the_fp64_criterion(hg, imf, eps):
     # the GPU's FMA-contracted interpolation differs from the oracle's in the last
     # bits; only a criterion within ~1e-15 of a power of two could decide otherwise
     assert mismatch <= max(1, checked // 100000), (mismatch, checked)
+
+
+def test_bind_device_state_lives_in_caller_tensors(hg):
+    """hg_bind_device: the caller's CUDA tensors become the state (copied in),
+    block steps update them in place bitwise like an unbound context, unbinding
+    copies the state back; binding without copy takes (checked) tensor contents;
+    host arrays are refused."""
+    import torch
+    n, eps = 2000, 1e-3
+    p = inputs.plummer(n, 41)
+    o = hg.hg_default_opts(precision=hg.HG_FP64, dt_max=DT_MAX)
+    a = hg.hg_init(p.mass, p.pos, p.vel, eps, 0.45, o)
+    b = hg.hg_init(p.mass, p.pos, p.vel, eps, 0.45, o)
+    c = hg.hg_init(p.mass, p.pos, p.vel, eps, 0.45, hg.hg_default_opts(precision=hg.HG_FP64, dt_max=DT_MAX,
+                                                                      start_mode=1))
+    try:
+        with pytest.raises(hg.HGError):
+            hg.hg_bind_device(a, hg.new_state(n))          # host memory
+        bufs = hg.new_state(n, like="cuda")
+        hg.hg_bind_device(a, bufs, copy_in=True)
+        ref, _ = gpu_state(hg, b, n)
+        for f in hg.STATE_FIELDS:
+            np.testing.assert_array_equal(bufs[f].cpu().numpy(), ref[f], err_msg=f)
+        hg.hg_step(a, 25)
+        hg.hg_step(b, 25)
+        torch.cuda.synchronize()
+        ref, t_ref = gpu_state(hg, b, n)
+        for f in hg.STATE_FIELDS:
+            np.testing.assert_array_equal(bufs[f].cpu().numpy(), ref[f], err_msg=f)
+        # a state written by the caller into unbound tensors, taken without copy
+        other = {f: bufs[f].clone() for f in hg.STATE_FIELDS}
+        hg.hg_bind_device(a, None)
+        got, t_got = gpu_state(hg, a, n)
+        assert t_got == t_ref
+        for f in hg.STATE_FIELDS:
+            np.testing.assert_array_equal(got[f], ref[f], err_msg=f)
+        hg.hg_bind_device(c, other, copy_in=False)
+        hg.hg_set_state(c, {f: ref[f] for f in hg.STATE_FIELDS}, t_ref)   # block time t_sys
+        for ctx in (a, b, c):
+            hg.hg_step(ctx, 5)
+        torch.cuda.synchronize()
+        ra, _ = gpu_state(hg, a, n)
+        rb, _ = gpu_state(hg, b, n)
+        for f in hg.STATE_FIELDS:
+            np.testing.assert_array_equal(ra[f], rb[f], err_msg=f)
+            np.testing.assert_array_equal(other[f].cpu().numpy(), rb[f], err_msg=f)
+        bad = {f: other[f].clone() for f in hg.STATE_FIELDS}
+        bad["dt"][0] = 0.3                                   # not a power of two
+        with pytest.raises(hg.HGError):
+            hg.hg_bind_device(c, bad, copy_in=False)
+    finally:
+        for ctx in (a, b, c):
+            hg.hg_free(ctx)
