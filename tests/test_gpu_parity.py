@@ -351,8 +351,12 @@ def test_kepler_orbit_zero_softening(hg):
         hg.hg_free(ctx)
 
 
-def test_single_particle(hg):
-    o = hg.hg_default_opts(dt_max=DT_MAX)
+@pytest.mark.parametrize("precision,order", [(0, 6), (1, 6), (0, 4), (1, 4)])
+def test_single_particle(hg, precision, order):
+    """Degenerate system: no forces, the criterion has a zero denominator
+    (infinite step, clamped to dt_max), free motion is exact; an empty
+    evaluation and correction (m = 0) are accepted."""
+    o = hg.hg_default_opts(dt_max=DT_MAX, precision=precision, order=order)
     ctx = hg.hg_init(np.array([1.0]), np.zeros((1, 3)), np.array([[0.5, 0.0, 0.0]]), 1e-3, 0.45, o)
     try:
         got, _ = gpu_state(hg, ctx, 1)
@@ -360,6 +364,11 @@ def test_single_particle(hg):
         hg.hg_advance(ctx, 0.5)
         got, t = gpu_state(hg, ctx, 1)
         assert t == 0.5 and got["pos"][0, 0] == pytest.approx(0.25, rel=1e-15)
+        assert got["dt"][0] == DT_MAX and np.all(got["acc"] == 0)
+        hg.hg_predict(ctx, 0.5)
+        hg.hg_evaluate(ctx, np.empty(0, dtype=np.int32), 0)
+        hg.hg_correct(ctx, None, 0)
+        assert gpu_state(hg, ctx, 1)[1] == 0.5
     finally:
         hg.hg_free(ctx)
 
