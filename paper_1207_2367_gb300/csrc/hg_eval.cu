@@ -164,12 +164,61 @@ struct Mixed {
         }
     }
 
-    __device__ static void finish(const Acc &a, double (&out)[I][9])
+    // Compensated pairs (true value hi - lo) added without rounding loss in hi:
+    // two-sum s + e = hi1 + hi2 exactly (Knuth), then lo = lo1 + lo2 - e.
+    __device__ __forceinline__ static void add_pair(float &hi, float &lo, float hi2, float lo2)
     {
+        const float s = hi + hi2;
+        const float bb = s - hi;
+        const float e = (hi - (s - bb)) + (hi2 - bb);
+        hi = s;
+        lo = (lo + lo2) - e;
+    }
+
+    // Sum the tpi lanes sharing an i-particle (fixed xor tree; shared memory
+    // across warps for tpi = 64) in FP32 pairs, then widen once: the leader lanes
+    // (lane_j == 0) hold out = hi - lo in FP64.  On GB300 an FP64 warp
+    // instruction costs ~64 cycles, so the tree stays in FP32 and the widening
+    // uses the integer f2d.
+    __device__ static void epilogue(Acc &a, int tpi, int tid, double *red, double (&out)[I][9])
+    {
+        const int wspan = tpi < 32 ? tpi : 32;
+        for (int off = 1; off < wspan; off <<= 1) {
+#pragma unroll
+            for (int k = 0; k < I; ++k)
+#pragma unroll
+                for (int c = 0; c < 9; ++c) {
+                    const float h2 = __shfl_xor_sync(0xffffffffu, a.hi[k][c], off);
+                    const float l2 = __shfl_xor_sync(0xffffffffu, a.lo[k][c], off);
+                    add_pair(a.hi[k][c], a.lo[k][c], h2, l2);
+                }
+        }
+        if (tpi > 32) {
+            float2 *r2 = reinterpret_cast<float2 *>(red);
+            const int warp = tid >> 5, lane = tid & 31, wpg = tpi >> 5;
+            if (lane == 0) {
+#pragma unroll
+                for (int k = 0; k < I; ++k)
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) r2[(warp * I + k) * 9 + c] = make_float2(a.hi[k][c], a.lo[k][c]);
+            }
+            __syncthreads();
+            if (lane == 0 && (warp % wpg) == 0) {
+#pragma unroll
+                for (int k = 0; k < I; ++k)
+#pragma unroll
+                    for (int c = 0; c < 9; ++c)
+                        for (int g = 1; g < wpg; ++g) {
+                            const float2 v = r2[((warp + g) * I + k) * 9 + c];
+                            add_pair(a.hi[k][c], a.lo[k][c], v.x, v.y);
+                        }
+            }
+            __syncthreads();
+        }
 #pragma unroll
         for (int k = 0; k < I; ++k)
 #pragma unroll
-            for (int c = 0; c < 9; ++c) out[k][c] = (double)a.hi[k][c] - (double)a.lo[k][c];
+            for (int c = 0; c < 9; ++c) out[k][c] = f2d(a.hi[k][c]) - f2d(a.lo[k][c]);
     }
 };
 
@@ -276,12 +325,42 @@ struct F64 {
         }
     }
 
-    __device__ static void finish(const Acc &a, double (&out)[I][9])
+    // Sum the tpi lanes sharing an i-particle (fixed xor tree; shared memory
+    // across warps for tpi = 64): the leader lanes (lane_j == 0) hold out.
+    __device__ static void epilogue(Acc &a, int tpi, int tid, double *red, double (&out)[I][9])
     {
 #pragma unroll
         for (int k = 0; k < I; ++k)
 #pragma unroll
             for (int c = 0; c < 9; ++c) out[k][c] = a.s[k][c];
+        const int wspan = tpi < 32 ? tpi : 32;
+        for (int off = 1; off < wspan; off <<= 1) {
+#pragma unroll
+            for (int k = 0; k < I; ++k)
+#pragma unroll
+                for (int c = 0; c < 9; ++c) out[k][c] += __shfl_xor_sync(0xffffffffu, out[k][c], off);
+        }
+        if (tpi > 32) {
+            const int warp = tid >> 5, lane = tid & 31, wpg = tpi >> 5;
+            if (lane == 0) {
+#pragma unroll
+                for (int k = 0; k < I; ++k)
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) red[(warp * I + k) * 9 + c] = out[k][c];
+            }
+            __syncthreads();
+            if (lane == 0 && (warp % wpg) == 0) {
+#pragma unroll
+                for (int k = 0; k < I; ++k)
+#pragma unroll
+                    for (int c = 0; c < 9; ++c) {
+                        double s = red[(warp * I + k) * 9 + c];
+                        for (int g = 1; g < wpg; ++g) s += red[((warp + g) * I + k) * 9 + c];
+                        out[k][c] = s;
+                    }
+            }
+            __syncthreads();
+        }
     }
 };
 
@@ -293,6 +372,40 @@ constexpr size_t smem_bytes()
 {
     return (size_t)kStages * P::kStageBytes + kStages * sizeof(uint64_t) +
            (kEvalThreads / 32) * P::I * 9 * sizeof(double);
+}
+
+// Sum the b chunk partials of positions [q0, q1) (rows q + s m of the [b][m][9]
+// buffer, s in chunk order) into ra/rj/rs, with the CTA's threads: one thread per
+// (position, component) for b <= 32, else one warp each (lane l sums chunks
+// l, l + 32, ..., then a fixed butterfly).  The same order as k_reduce, so the
+// results are the same bits.  Partials written by other CTAs are read through L2.
+__device__ __noinline__ void reduce_rows(const EvalArgs &args, int64_t q0, int64_t q1, int64_t m, int b, double *ra,
+                                         double *rj, double *rs)
+{
+    const int64_t total = (q1 - q0) * 9;
+    if (b <= 32) {
+        for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+            const int64_t q = q0 + e / 9;
+            const int c = (int)(e % 9);
+            double s = 0.0;
+            for (int sp = 0; sp < b; ++sp) s += __ldcg(args.partial + ((int64_t)sp * m + q) * 9 + c);
+            double *dst = c < 3 ? ra : (c < 6 ? rj : rs);
+            dst[q * 3 + (c % 3)] = s;
+        }
+        return;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t e = warp; e < total; e += nw) {
+        const int64_t q = q0 + e / 9;
+        const int c = (int)(e % 9);
+        double s = 0.0;
+        for (int sp = lane; sp < b; sp += 32) s += __ldcg(args.partial + ((int64_t)sp * m + q) * 9 + c);
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) {
+            double *dst = c < 3 ? ra : (c < 6 ? rj : rs);
+            dst[q * 3 + (c % 3)] = s;
+        }
+    }
 }
 
 template <class P, bool GUARD>
@@ -407,34 +520,20 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
         seq += (uint32_t)nt;
 
         double out[P::I][9];
-        P::finish(acc, out);
-        const int wspan = tpi < 32 ? tpi : 32;
-        for (int off = 1; off < wspan; off <<= 1) {
-#pragma unroll
-            for (int k = 0; k < P::I; ++k)
-#pragma unroll
-                for (int c = 0; c < 9; ++c) out[k][c] += __shfl_xor_sync(0xffffffffu, out[k][c], off);
-        }
-        if (tpi > 32) {
-            const int warp = tid >> 5, lane = tid & 31, wpg = tpi >> 5;
-            if (lane == 0) {
+        P::epilogue(acc, tpi, tid, red, out);
+        const bool fused = !batch && args.tile_cnt != nullptr;
+        if (fused && pl.b == 1) {   // no j-split: these are the results
+            if (lane_j == 0) {
 #pragma unroll
                 for (int k = 0; k < P::I; ++k)
+                    if (qi[k] < q_end)
 #pragma unroll
-                    for (int c = 0; c < 9; ++c) red[(warp * P::I + k) * 9 + c] = out[k][c];
+                        for (int c = 0; c < 9; ++c) {
+                            double *dst = c < 3 ? args.ra : (c < 6 ? args.rj : args.rs);
+                            dst[qi[k] * 3 + c % 3] = out[k][c];
+                        }
             }
-            __syncthreads();
-            if (lane == 0 && (warp % wpg) == 0) {
-#pragma unroll
-                for (int k = 0; k < P::I; ++k)
-#pragma unroll
-                    for (int c = 0; c < 9; ++c) {
-                        double s = red[(warp * P::I + k) * 9 + c];
-                        for (int g = 1; g < wpg; ++g) s += red[((warp + g) * P::I + k) * 9 + c];
-                        out[k][c] = s;
-                    }
-            }
-            __syncthreads();
+            continue;
         }
         if (lane_j == 0) {
 #pragma unroll
@@ -444,6 +543,25 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
 #pragma unroll
                     for (int c = 0; c < 9; ++c) dst[c] = out[k][c];
                 }
+            }
+        }
+        if (fused) {
+            // The last CTA to finish this i-tile sums its b partials (arrival
+            // count, no waiting; the counter is reset for the next launch).
+            __shared__ int s_last;
+            const int64_t itile = item / pl.b;
+            __threadfence();   // this thread's partials, before the arrival below
+            __syncthreads();
+            if (tid == 0) {
+                const int old = atomicAdd(&args.tile_cnt[itile], 1);
+                s_last = old == pl.b - 1;
+                if (s_last) args.tile_cnt[itile] = 0;
+            }
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                const int64_t q1 = q_tile + pl.ti < m ? q_tile + pl.ti : m;
+                reduce_rows(args, q_tile, q1, m, pl.b, args.ra, args.rj, args.rs);
             }
         }
     }

@@ -232,6 +232,12 @@ struct EvalArgs {
     uint32_t tx_extra;       // testing: bytes expected per tile beyond those copied (0 normally)
     int32_t *err;
     BatchView bv;            // clusters (bv.nc == 0: single system)
+    // One system: the j-split reduction inside the evaluation.  The last CTA to
+    // finish an i-tile (arrival count tile_cnt[i-tile], reset by that CTA) sums
+    // the tile's b partials in chunk order into ra/rj/rs [m][3]; b = 1 writes
+    // them directly.  tile_cnt == nullptr: partials only (k_reduce sums them).
+    int32_t *tile_cnt;
+    double *ra, *rj, *rs;
 };
 
 // Planner inputs of one precision (hg_eval.cu): tiles, tile size, i per thread,
@@ -321,6 +327,35 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
             smem_addr(dst)),
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
+}
+
+// FP64 <-> FP32 conversions done with integer operations on the IEEE-754
+// encodings (binary64: 1 sign, 11 exponent bits, bias 1023, 52 fraction bits;
+// binary32: 1, 8, bias 127, 23).  GB300's FP64 pipe, which also executes the
+// hardware conversions, is the predictor's limit; the integer pipes are not.
+// d2f: round to nearest, ties to even; results below the smallest normal float
+// (2^-126) become zero of the same sign.  Inputs are finite.
+__device__ __forceinline__ float d2f(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7ffu) - 1023 + 127;
+    unsigned int m = (unsigned int)((b >> 29) & 0x7fffffu);
+    const unsigned int rem = (unsigned int)b & 0x1fffffffu;
+    m += (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;   // may carry into e
+    const unsigned int mag = ((unsigned int)e << 23) + m;
+    return __uint_as_float(e <= 0 ? sign : (sign | mag));
+}
+
+// Exact widening of a float that is zero or normal.
+__device__ __forceinline__ double f2d(float f)
+{
+    const unsigned int u = __float_as_uint(f);
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    const unsigned int e = (u >> 23) & 0xffu;
+    const unsigned long long mag =
+        ((unsigned long long)(e + (1023u - 127u)) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)(e == 0u ? sign : (sign | mag)));
 }
 
 // Hardware reciprocal square root (single MUFU instruction, flush-to-zero).
