@@ -184,18 +184,18 @@ __host__ __device__ inline Plan make_plan(int64_t m, const PlanParams &q)
 // j-tile of a cluster starts on a tile boundary.  The per-step arrays form the
 // work list written by the batch planning kernel.
 struct BatchView {
-    int32_t nc;
-    const int64_t *cl_off;   // [nc+1] particle offsets
-    const int64_t *rec_off;  // [nc+1] record offsets (multiples of 256)
-    const int32_t *rmap;     // [n] record index of each particle
-    const int32_t *cl_of;    // [n] cluster of each particle
-    int64_t *a_off;          // [nc+1] first position of each cluster in the active list
-    int64_t *item_off;       // [nc+1] first work item of each cluster
-    int64_t *part_off;       // [nc+1] first partial-sum row of each cluster
-    int64_t *pred_off;       // [nc+1] prefix of the sizes of clusters with active particles
-    int32_t *tpi_c;          // [nc] threads per i-particle
-    int32_t *b_c;            // [nc] j-chunks
-    int64_t *tps;            // [1] tiles per j-chunk
+    int32_t nc = 0;
+    const int64_t *cl_off = nullptr;   // [nc+1] particle offsets
+    const int64_t *rec_off = nullptr;  // [nc+1] record offsets (multiples of 256)
+    const int32_t *rmap = nullptr;     // [n] record index of each particle
+    const int32_t *cl_of = nullptr;    // [n] cluster of each particle
+    int64_t *a_off = nullptr;          // [nc+1] first position of each cluster in the active list
+    int64_t *item_off = nullptr;       // [nc+1] first work item of each cluster
+    int64_t *part_off = nullptr;       // [nc+1] first partial-sum row of each cluster
+    int64_t *pred_off = nullptr;       // [nc+1] prefix of the sizes of clusters with active particles
+    int32_t *tpi_c = nullptr;          // [nc] threads per i-particle
+    int32_t *b_c = nullptr;            // [nc] j-chunks
+    int64_t *tps = nullptr;            // [1] tiles per j-chunk
 };
 
 constexpr int kBatchTpsMax = 64;   // tiles per j-chunk considered by the batch planner
@@ -219,25 +219,25 @@ __host__ __device__ inline BatchKnobs batch_knobs(int64_t m, const PlanParams &q
 }
 
 struct EvalArgs {
-    Records rec;
-    int64_t npad;
-    const int32_t *idx;      // active list (device)
-    const int64_t *m_dev;    // block size on the device (graph mode), or nullptr
-    int64_t m_host;          // block size when m_dev == nullptr
-    const Plan *plan_dev;    // plan on the device (graph mode), or nullptr
-    Plan plan_host;          // plan when plan_dev == nullptr
-    double *partial;         // [b][m][9] partial sums
-    double eps2;
-    int guard;               // eps == 0: skip r^2 == 0 pairs
-    uint32_t tx_extra;       // testing: bytes expected per tile beyond those copied (0 normally)
-    int32_t *err;
-    BatchView bv;            // clusters (bv.nc == 0: single system)
+    Records rec{};
+    int64_t npad = 0;
+    const int32_t *idx = nullptr;      // active list (device)
+    const int64_t *m_dev = nullptr;    // block size on the device (graph mode), or nullptr
+    int64_t m_host = 0;                // block size when m_dev == nullptr
+    const Plan *plan_dev = nullptr;    // plan on the device (graph mode), or nullptr
+    Plan plan_host{};                  // plan when plan_dev == nullptr
+    double *partial = nullptr;         // [b][m][9] partial sums
+    double eps2 = 0.0;
+    int guard = 0;                     // eps == 0: skip r^2 == 0 pairs
+    uint32_t tx_extra = 0;             // testing: bytes expected per tile beyond those copied (0 normally)
+    int32_t *err = nullptr;
+    BatchView bv{};                    // clusters (bv.nc == 0: single system)
     // One system: the j-split reduction inside the evaluation.  The last CTA to
     // finish an i-tile (arrival count tile_cnt[i-tile], reset by that CTA) sums
     // the tile's b partials in chunk order into ra/rj/rs [m][3]; b = 1 writes
     // them directly.  tile_cnt == nullptr: partials only (k_reduce sums them).
-    int32_t *tile_cnt;
-    double *ra, *rj, *rs;
+    int32_t *tile_cnt = nullptr;
+    double *ra = nullptr, *rj = nullptr, *rs = nullptr;
 };
 
 // Planner inputs of one precision (hg_eval.cu): tiles, tile size, i per thread,

@@ -220,7 +220,8 @@ extern "C" int hg_evaluate_static(int64_t n, const double *mass, const double *p
     else
         k_pack<false><<<blocks, threads, 0, st>>>(n, npad, mass, pos, vel, acc_pred, rec);
 
-    EvalArgs a;
+    EvalArgs a{};           // every field zero unless set below (one system: bv.nc = 0)
+    a.bv = BatchView{};
     a.rec = rec;
     a.npad = npad;
     a.idx = idx;
