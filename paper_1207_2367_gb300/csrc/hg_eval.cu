@@ -378,7 +378,8 @@ constexpr size_t smem_bytes()
 // buffer, s in chunk order) into ra/rj/rs, with the CTA's threads: one thread per
 // (position, component) for b <= 32, else one warp each (lane l sums chunks
 // l, l + 32, ..., then a fixed butterfly).  The same order as k_reduce, so the
-// results are the same bits.  Partials written by other CTAs are read through L2.
+// results are the same bits.  Partials written by other CTAs are fetched afresh
+// (ld.global.cv) after the arrival count and fences of the caller.
 __device__ __noinline__ void reduce_rows(const EvalArgs &args, int64_t q0, int64_t q1, int64_t m, int b, double *ra,
                                          double *rj, double *rs)
 {
@@ -388,7 +389,7 @@ __device__ __noinline__ void reduce_rows(const EvalArgs &args, int64_t q0, int64
             const int64_t q = q0 + e / 9;
             const int c = (int)(e % 9);
             double s = 0.0;
-            for (int sp = 0; sp < b; ++sp) s += __ldcg(args.partial + ((int64_t)sp * m + q) * 9 + c);
+            for (int sp = 0; sp < b; ++sp) s += __ldcv(args.partial + ((int64_t)sp * m + q) * 9 + c);
             double *dst = c < 3 ? ra : (c < 6 ? rj : rs);
             dst[q * 3 + (c % 3)] = s;
         }
@@ -399,7 +400,7 @@ __device__ __noinline__ void reduce_rows(const EvalArgs &args, int64_t q0, int64
         const int64_t q = q0 + e / 9;
         const int c = (int)(e % 9);
         double s = 0.0;
-        for (int sp = lane; sp < b; sp += 32) s += __ldcg(args.partial + ((int64_t)sp * m + q) * 9 + c);
+        for (int sp = lane; sp < b; sp += 32) s += __ldcv(args.partial + ((int64_t)sp * m + q) * 9 + c);
         for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
         if (lane == 0) {
             double *dst = c < 3 ? ra : (c < 6 ? rj : rs);
@@ -555,7 +556,10 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
             if (tid == 0) {
                 const int old = atomicAdd(&args.tile_cnt[itile], 1);
                 s_last = old == pl.b - 1;
-                if (s_last) args.tile_cnt[itile] = 0;
+                if (s_last) {
+                    args.tile_cnt[itile] = 0;
+                    __threadfence();   // the other CTAs' partials, before the barrier below
+                }
             }
             __syncthreads();
             if (s_last) {

@@ -412,7 +412,12 @@ __global__ void __launch_bounds__(64) k_predict_select(const State st, const Rec
     }
     if (!last_to_arrive(&sc->arrive[2], gridDim.x, &last)) return;
     __threadfence();
-    const int64_t m = (int64_t)*((volatile uint32_t *)&sc->slot);
+    // One read of the slot count, shared before thread 0 resets it (a thread
+    // reading it after the reset would score the plan for another m).
+    __shared__ int64_t s_m;
+    if (threadIdx.x == 0) s_m = (int64_t)*((volatile uint32_t *)&sc->slot);
+    __syncthreads();
+    const int64_t m = s_m;
     if (threadIdx.x == 0) {
         sc->m = m;
         sc->t_cur = t_next;

@@ -241,3 +241,27 @@ def test_bind_device_state_lives_in_caller_tensors(hg):
     finally:
         for ctx in (a, b, c):
             hg.hg_free(ctx)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_identical_contexts_stay_bitwise_identical(hg, precision):
+    """Determinism: two contexts with the same input take 200 graph-replayed
+    block steps (every block size of the early integration, evaluation with the
+    j-split reduction inside, unordered active lists) and end with the same
+    bits in every state field."""
+    n, eps = 4096, 1e-4
+    p = inputs.plummer(n, 77)
+    o = hg.hg_default_opts(precision=precision, dt_max=DT_MAX)
+    a = hg.hg_init(p.mass, p.pos, p.vel, eps, 0.45, o)
+    b = hg.hg_init(p.mass, p.pos, p.vel, eps, 0.45, o)
+    try:
+        hg.hg_step(a, 200)
+        hg.hg_step(b, 200)
+        sa, ta = gpu_state(hg, a, n)
+        sb, tb = gpu_state(hg, b, n)
+        assert ta == tb
+        for f in hg.STATE_FIELDS:
+            np.testing.assert_array_equal(sa[f], sb[f], err_msg=f)
+    finally:
+        hg.hg_free(a)
+        hg.hg_free(b)
