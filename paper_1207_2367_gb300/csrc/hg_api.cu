@@ -34,7 +34,6 @@ struct hg_ctx {
     DevScalars *d_sc = nullptr, *h_sc = nullptr;   // h_sc: pinned host mirror
     double *h_stage = nullptr;                     // pinned staging for small uploads
     double *partial = nullptr;
-    int32_t *tile_cnt = nullptr;   // arrival counts of the fused j-split reduction (one system)
     int64_t pcap = 0;
     PlanParams pp{};      // evaluation planner inputs
     BatchView bv{};       // independent clusters (bv.nc == 0: one system)
@@ -149,8 +148,7 @@ EvalArgs eval_args(hg_ctx *c, const int64_t *m_dev, int64_t m_host)
     a.tx_extra = c->opts.test_stall_eval ? 16u : 0u;
     a.err = &c->d_sc->err;
     a.bv = c->bv;
-    const bool fused = c->bv.nc == 0;   // one system: the evaluation also sums the j-split partials
-    a.tile_cnt = fused ? c->tile_cnt : nullptr;
+    a.direct_b1 = c->bv.nc == 0 ? 1 : 0;   // one system: b = 1 plans write the results directly
     a.ra = c->ra;
     a.rj = c->rj;
     a.rs = c->rs;
@@ -174,11 +172,8 @@ int run_eval_host_m(hg_ctx *c, int64_t m)
         c->kernels += 1;
     }
     HG_CUDA(c, launch_eval(c->mixed, a, c->num_sms, c->stream));
-    c->kernels += 1;
-    if (!a.tile_cnt) {
-        HG_CUDA(c, launch_reduce(a, c->ra, c->rj, c->rs, 2 * c->num_sms, c->stream));
-        c->kernels += 1;
-    }
+    HG_CUDA(c, launch_reduce(a, c->ra, c->rj, c->rs, 2 * c->num_sms, c->stream));
+    c->kernels += 2;
     return HG_OK;
 }
 
@@ -213,10 +208,10 @@ int upload_scalar(hg_ctx *c, double *dev_field, double v)
 }
 
 // Kernels per graph-replayed block step: one system, selection + prediction,
-// evaluation with the j-split reduction (mixed: both kernel variants, one
-// returns at once), correction (with the next minimum); clusters, three
-// next-block passes, batch plan, prediction, evaluation, reduction, correction.
-int step_kernels(const hg_ctx *c) { return c->bv.nc > 0 ? 8 : (c->mixed ? 4 : 3); }
+// evaluation (mixed: both kernel variants, one returns at once), reduction,
+// correction (with the next minimum); clusters, three next-block passes, batch
+// plan, prediction, evaluation, reduction, correction.
+int step_kernels(const hg_ctx *c) { return c->bv.nc > 0 ? 8 : (c->mixed ? 5 : 4); }
 
 // An event record that becomes a graph node when the stream is being captured
 // (a plain record inside a capture only orders work and cannot be timed).
@@ -247,7 +242,7 @@ int enqueue_block_step(hg_ctx *c, cudaStream_t s, const cudaEvent_t *ev)
     EvalArgs a = eval_args(c, &c->d_sc->m, 0);
     HG_CUDA(c, launch_eval(c->mixed, a, c->num_sms, s));
     if (ev) HG_CUDA(c, record_external(ev[3], s));
-    if (!a.tile_cnt) HG_CUDA(c, launch_reduce(a, c->ra, c->rj, c->rs, 2 * c->num_sms, s));
+    HG_CUDA(c, launch_reduce(a, c->ra, c->rj, c->rs, 2 * c->num_sms, s));
     if (ev) HG_CUDA(c, record_external(ev[4], s));
     HG_CUDA(c, launch_correct(c->st, c->d_idx, &c->d_sc->m, 0, c->n, c->ra, c->rj, c->rs, step_params(c), c->d_sc,
                               batch ? 0 : 1, 2 * c->num_sms, s));
@@ -449,7 +444,6 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
         bv.cl_of = co;
     }
     c->partial = dalloc<double>(c, 9 * pcap);
-    c->tile_cnt = dalloc<int32_t>(c, n / 2 + 2);   // i-tiles hold >= 2 particles
     c->ra = dalloc<double>(c, 3 * n);
     c->rj = dalloc<double>(c, 3 * n);
     c->rs = dalloc<double>(c, 3 * n);
@@ -462,8 +456,8 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
     c->e_out = dalloc<double>(c, 2);
     c->l_part = dalloc<double>(c, 3 * c->e_g2);
     c->l_out = dalloc<double>(c, 3);
-    ok = ok && c->d_idx && c->d_idx2 && c->nb_part && c->nb_cnt && c->nb_off && c->d_sc && c->partial && c->tile_cnt &&
-         c->ra && c->rj &&
+    ok = ok && c->d_idx && c->d_idx2 && c->nb_part && c->nb_cnt && c->nb_off && c->d_sc && c->partial && c->ra &&
+         c->rj &&
          c->rs && c->xe && c->ve && c->phi_part && c->e_part && c->e_out && c->l_part && c->l_out;
     if (!ok) return fail(c, HG_ENOMEM, "device allocation failed");
 
@@ -475,7 +469,6 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
     z.t_stop = INFINITY;
     *c->h_sc = z;
     HG_CUDA(c, cudaMemcpyAsync(c->d_sc, c->h_sc, sizeof(DevScalars), cudaMemcpyHostToDevice, c->stream));
-    HG_CUDA(c, cudaMemsetAsync(c->tile_cnt, 0, (size_t)(n / 2 + 2) * sizeof(int32_t), c->stream));
     HG_CUDA(c, cudaMemcpyAsync(c->st.mass, mass, n * sizeof(double), cudaMemcpyDefault, c->stream));
     HG_CUDA(c, cudaMemcpyAsync(c->st.x, pos, 3 * n * sizeof(double), cudaMemcpyDefault, c->stream));
     HG_CUDA(c, cudaMemcpyAsync(c->st.v, vel, 3 * n * sizeof(double), cudaMemcpyDefault, c->stream));

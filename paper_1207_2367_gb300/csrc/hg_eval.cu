@@ -374,41 +374,6 @@ constexpr size_t smem_bytes()
            (kEvalThreads / 32) * P::I * 9 * sizeof(double);
 }
 
-// Sum the b chunk partials of positions [q0, q1) (rows q + s m of the [b][m][9]
-// buffer, s in chunk order) into ra/rj/rs, with the CTA's threads: one thread per
-// (position, component) for b <= 32, else one warp each (lane l sums chunks
-// l, l + 32, ..., then a fixed butterfly).  The same order as k_reduce, so the
-// results are the same bits.  Partials written by other CTAs are fetched afresh
-// (ld.global.cv) after the arrival count and fences of the caller.
-__device__ __noinline__ void reduce_rows(const EvalArgs &args, int64_t q0, int64_t q1, int64_t m, int b, double *ra,
-                                         double *rj, double *rs)
-{
-    const int64_t total = (q1 - q0) * 9;
-    if (b <= 32) {
-        for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
-            const int64_t q = q0 + e / 9;
-            const int c = (int)(e % 9);
-            double s = 0.0;
-            for (int sp = 0; sp < b; ++sp) s += __ldcv(args.partial + ((int64_t)sp * m + q) * 9 + c);
-            double *dst = c < 3 ? ra : (c < 6 ? rj : rs);
-            dst[q * 3 + (c % 3)] = s;
-        }
-        return;
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int64_t e = warp; e < total; e += nw) {
-        const int64_t q = q0 + e / 9;
-        const int c = (int)(e % 9);
-        double s = 0.0;
-        for (int sp = lane; sp < b; sp += 32) s += __ldcv(args.partial + ((int64_t)sp * m + q) * 9 + c);
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (lane == 0) {
-            double *dst = c < 3 ? ra : (c < 6 ? rj : rs);
-            dst[q * 3 + (c % 3)] = s;
-        }
-    }
-}
-
 template <class P, bool GUARD>
 __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const EvalArgs args)
 {
@@ -522,8 +487,7 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
 
         double out[P::I][9];
         P::epilogue(acc, tpi, tid, red, out);
-        const bool fused = !batch && args.tile_cnt != nullptr;
-        if (fused && pl.b == 1) {   // no j-split: these are the results
+        if (!batch && args.direct_b1 && pl.b == 1) {   // no j-split: these are the results
             if (lane_j == 0) {
 #pragma unroll
                 for (int k = 0; k < P::I; ++k)
@@ -546,28 +510,6 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
                 }
             }
         }
-        if (fused) {
-            // The last CTA to finish this i-tile sums its b partials (arrival
-            // count, no waiting; the counter is reset for the next launch).
-            __shared__ int s_last;
-            const int64_t itile = item / pl.b;
-            __threadfence();   // this thread's partials, before the arrival below
-            __syncthreads();
-            if (tid == 0) {
-                const int old = atomicAdd(&args.tile_cnt[itile], 1);
-                s_last = old == pl.b - 1;
-                if (s_last) {
-                    args.tile_cnt[itile] = 0;
-                    __threadfence();   // the other CTAs' partials, before the barrier below
-                }
-            }
-            __syncthreads();
-            if (s_last) {
-                __threadfence();
-                const int64_t q1 = q_tile + pl.ti < m ? q_tile + pl.ti : m;
-                reduce_rows(args, q_tile, q1, m, pl.b, args.ra, args.rj, args.rs);
-            }
-        }
     }
 }
 
@@ -578,6 +520,7 @@ __global__ void k_reduce(const EvalArgs args, double *ra, double *rj, double *rs
     const int64_t m = args.m_dev ? *args.m_dev : args.m_host;
     if (m <= 0) return;
     const Plan pl = args.plan_dev ? *args.plan_dev : args.plan_host;
+    if (args.bv.nc == 0 && args.direct_b1 && pl.b == 1) return;   // the evaluation wrote the results
     const int64_t total = m * 9;
     if (args.bv.nc > 0) {
         // Clusters: the chunks of position q are rows part_off[c] + s * m_c + (q - a_off[c]).

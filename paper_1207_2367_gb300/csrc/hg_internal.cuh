@@ -232,11 +232,10 @@ struct EvalArgs {
     uint32_t tx_extra = 0;             // testing: bytes expected per tile beyond those copied (0 normally)
     int32_t *err = nullptr;
     BatchView bv{};                    // clusters (bv.nc == 0: single system)
-    // One system: the j-split reduction inside the evaluation.  The last CTA to
-    // finish an i-tile (arrival count tile_cnt[i-tile], reset by that CTA) sums
-    // the tile's b partials in chunk order into ra/rj/rs [m][3]; b = 1 writes
-    // them directly.  tile_cnt == nullptr: partials only (k_reduce sums them).
-    int32_t *tile_cnt = nullptr;
+    // One system: a plan without j-split (b = 1) writes its sums straight into
+    // ra/rj/rs [m][3] and the reduction kernel returns at once (direct_b1 = 1);
+    // otherwise partials go to [b][m][9] and the reduction kernel sums them.
+    int direct_b1 = 0;
     double *ra = nullptr, *rj = nullptr, *rs = nullptr;
 };
 

@@ -235,8 +235,7 @@ extern "C" int hg_evaluate_static(int64_t n, const double *mass, const double *p
     a.guard = eps == 0.0 ? 1 : 0;
     a.tx_extra = 0;
     a.err = err;
-    a.tile_cnt = nullptr;   // partials summed by k_reduce
-    a.ra = a.rj = a.rs = nullptr;
+    a.direct_b1 = 0;        // partials summed by k_reduce
     if (cudaGetLastError() != cudaSuccess || launch_eval(mixed, a, slot->sms, st) != cudaSuccess ||
         launch_reduce(a, acc, jerk, snap, 2 * slot->sms, st) != cudaSuccess) {
         set_call_error("launch failed");
