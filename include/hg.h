@@ -261,7 +261,7 @@ int hg_evaluate_static(int64_t n, const double *mass, const double *pos, const d
 
 /* One bucket measured by hg_tune. */
 typedef struct hg_tune_entry {
-    int64_t m;           /* block size timed: the m particles with the smallest steps */
+    int64_t m;           /* middle block size timed (the m particles with the smallest steps) */
     int32_t bucket;      /* floor(log2 m) */
     int32_t candidates;  /* plans timed */
     int32_t model;       /* the cost model's choice, in table encoding */
@@ -271,10 +271,14 @@ typedef struct hg_tune_entry {
 } hg_tune_entry;
 
 /* Measure, for every bucket whose m is at most m_max (0: n; the m of bucket k is
- * 2^k for k = 0 and floor(1.5 * 2^k) clamped to n above), the cost model's plan
- * and its cheapest rivals on the context's current predicted data, with CUDA
- * events on the context's stream, each plan launched reps times (0: automatic)
- * after one warm-up; store a rival only if it is at least 3% faster.  The
+ * 1 for k = 0 and 1.5 * 2^k clamped to n above), the cost model's plan and its
+ * cheapest rivals on the context's current predicted data, with CUDA events on
+ * the context's stream, each plan launched reps times (0: automatic) after one
+ * warm-up.  Because one stored plan serves the whole bucket, every plan is timed
+ * at the bucket's block sizes 2 and 3 (k = 1) or 2^k * 5/4, 3/2 and 7/4 (k >= 2),
+ * clamped to n, and the times are summed; a rival is stored only if its sum is
+ * at least 3% below the cost model's.  model_us and best_us report the mean
+ * over those block sizes.  The
  * integration state is unchanged, a pending hg_evaluate is dropped and the
  * captured graphs are rebuilt on their next use.  report (capacity cap, may be
  * NULL) receives one entry per bucket measured; *n_out their number.

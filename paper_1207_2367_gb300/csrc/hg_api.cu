@@ -39,6 +39,7 @@ struct hg_ctx {
     BatchView bv{};       // independent clusters (bv.nc == 0: one system)
     std::vector<int64_t> cl_off_host;
     double *ra = nullptr, *rj = nullptr, *rs = nullptr;
+    double *rn = nullptr;   // [n] noise scale of the evaluated particles (mixed)
     double *xe = nullptr, *ve = nullptr, *phi_part = nullptr, *e_part = nullptr, *e_out = nullptr;
     double *l_part = nullptr, *l_out = nullptr;   // angular momentum: 3 partials per CTA, result
     int e_splits = 0, e_g2 = 0;
@@ -124,8 +125,10 @@ StepParams step_params(const hg_ctx *c)
     p.eta_init = c->opts.eta_init;
     p.dt_min = c->opts.dt_min;
     p.dt_max = c->opts.dt_max;
-    // FP32 pair arithmetic resolves accelerations to ~1e-7 relative; a change
-    // below 3e-6 |a| carries no usable higher-derivative information.
+    // FP32 pair terms carry ~3e-7 relative rounding, so the evaluated a_i errs
+    // by up to ~3e-7 sum_j |a_ij|; a change below 3e-6 of the noise scale
+    // sum_j m_j / r_ij^2 (>= sum_j |a_ij|) carries no usable higher-derivative
+    // information.
     p.noise_rel = c->mixed ? 3e-6 : 0.0;
     p.log2_eta = (float)log2(c->eta);
     p.order = c->opts.order;
@@ -152,6 +155,7 @@ EvalArgs eval_args(hg_ctx *c, const int64_t *m_dev, int64_t m_host)
     a.ra = c->ra;
     a.rj = c->rj;
     a.rs = c->rs;
+    a.rn = c->mixed ? c->rn : nullptr;
     return a;
 }
 
@@ -244,8 +248,8 @@ int enqueue_block_step(hg_ctx *c, cudaStream_t s, const cudaEvent_t *ev)
     if (ev) HG_CUDA(c, record_external(ev[3], s));
     HG_CUDA(c, launch_reduce(a, c->ra, c->rj, c->rs, 2 * c->num_sms, s));
     if (ev) HG_CUDA(c, record_external(ev[4], s));
-    HG_CUDA(c, launch_correct(c->st, c->d_idx, &c->d_sc->m, 0, c->n, c->ra, c->rj, c->rs, step_params(c), c->d_sc,
-                              batch ? 0 : 1, 2 * c->num_sms, s));
+    HG_CUDA(c, launch_correct(c->st, c->d_idx, &c->d_sc->m, 0, c->n, c->ra, c->rj, c->rs, a.rn, step_params(c),
+                              c->d_sc, batch ? 0 : 1, 2 * c->num_sms, s));
     if (ev) HG_CUDA(c, record_external(ev[5], s));
     return HG_OK;
 }
@@ -443,10 +447,11 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
         bv.rmap = rm;
         bv.cl_of = co;
     }
-    c->partial = dalloc<double>(c, 9 * pcap);
+    c->partial = dalloc<double>(c, (int64_t)kOut * pcap);
     c->ra = dalloc<double>(c, 3 * n);
     c->rj = dalloc<double>(c, 3 * n);
     c->rs = dalloc<double>(c, 3 * n);
+    c->rn = dalloc<double>(c, n);
     c->xe = dalloc<double>(c, 3 * n);
     c->ve = dalloc<double>(c, 3 * n);
     c->e_splits = energy_splits(n, c->num_sms);
@@ -456,7 +461,7 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
     c->e_out = dalloc<double>(c, 2);
     c->l_part = dalloc<double>(c, 3 * c->e_g2);
     c->l_out = dalloc<double>(c, 3);
-    ok = ok && c->d_idx && c->d_idx2 && c->nb_part && c->nb_cnt && c->nb_off && c->d_sc && c->partial && c->ra &&
+    ok = ok && c->d_idx && c->d_idx2 && c->nb_part && c->nb_cnt && c->nb_off && c->d_sc && c->partial && c->ra && c->rn &&
          c->rj &&
          c->rs && c->xe && c->ve && c->phi_part && c->e_part && c->e_out && c->l_part && c->l_out;
     if (!ok) return fail(c, HG_ENOMEM, "device allocation failed");
@@ -609,32 +614,41 @@ int tune_impl(hg_ctx *c, int64_t m_max, int32_t reps_in, hg_tune_entry *report, 
     int32_t count = 0;
     std::vector<int32_t> list;
     for (int k = 0; k <= tune_bucket(mtop) && rc == HG_OK; ++k) {
+        // A fixed plan serves the whole bucket, and its wave count jumps with
+        // m, so it is timed at block sizes spread over the bucket: 2^k (5/4,
+        // 3/2, 7/4), clamped to mtop; the reported m is the middle one.
         const int64_t m = k == 0 ? 1 : std::min<int64_t>(mtop, (int64_t)3 << (k - 1));
-        list.assign(order.begin(), order.begin() + m);
-        std::sort(list.begin(), list.end());
-        if (cudaMemcpyAsync(c->d_idx, list.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(c->stream) != cudaSuccess) {
-            rc = fail(c, HG_ECUDA, "list upload failed");
-            break;
-        }
+        std::vector<int64_t> pts;
+        if (k == 0) pts = {1};
+        else if (k == 1) pts = {2, std::min<int64_t>(mtop, 3)};
+        else
+            for (int64_t f = 5; f <= 7; ++f) pts.push_back(std::min<int64_t>(mtop, (f << k) / 4));
+        pts.erase(std::unique(pts.begin(), pts.end()), pts.end());
         const std::vector<int> cand = tune_candidates(c, m);
-        int reps = reps_in;
-        double model_us = 0.0, best_us = 0.0;
-        int best = -1;
-        for (size_t q = 0; q < cand.size() && rc == HG_OK; ++q) {
-            c->pp.tuned[k] = q == 0 ? -1 : (int16_t)cand[q];   // q == 0: the cost model itself
-            double us = 0.0;
-            rc = time_eval(c, m, &reps, e0, e1, &us);
-            if (q == 0) {
-                model_us = best_us = us;
-            } else if (us < best_us) {
-                best_us = us;
-                best = cand[q];
+        std::vector<double> sum(cand.size(), 0.0);
+        for (size_t pi = 0; pi < pts.size() && rc == HG_OK; ++pi) {
+            const int64_t mp = pts[pi];
+            list.assign(order.begin(), order.begin() + mp);
+            std::sort(list.begin(), list.end());
+            if (cudaMemcpyAsync(c->d_idx, list.data(), mp * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(c->stream) != cudaSuccess) {
+                rc = fail(c, HG_ECUDA, "list upload failed");
+                break;
+            }
+            int reps = reps_in;
+            for (size_t q = 0; q < cand.size() && rc == HG_OK; ++q) {
+                c->pp.tuned[k] = q == 0 ? -1 : (int16_t)cand[q];   // q == 0: the cost model itself
+                double us = 0.0;
+                rc = time_eval(c, mp, &reps, e0, e1, &us);
+                sum[q] += us;
             }
         }
         if (rc) break;
-        const int chosen = (best >= 0 && best_us < kTuneGain * model_us) ? best : -1;
+        size_t best = 0;
+        for (size_t q = 1; q < cand.size(); ++q)
+            if (sum[q] < sum[best]) best = q;
+        const int chosen = (best > 0 && sum[best] < kTuneGain * sum[0]) ? cand[best] : -1;
         c->pp.tuned[k] = (int16_t)chosen;
         if (report && count < cap) {
             hg_tune_entry &e = report[count];
@@ -643,8 +657,8 @@ int tune_impl(hg_ctx *c, int64_t m_max, int32_t reps_in, hg_tune_entry *report, 
             e.candidates = (int32_t)cand.size();
             e.model = cand[0];
             e.chosen = chosen;
-            e.model_us = model_us;
-            e.best_us = chosen >= 0 ? best_us : model_us;
+            e.model_us = sum[0] / (double)pts.size();
+            e.best_us = chosen >= 0 ? sum[best] / (double)pts.size() : e.model_us;
         }
         ++count;
     }
@@ -855,8 +869,8 @@ int hg_correct(hg_ctx *c, const int32_t *idx, int64_t m)
         return fail(c, HG_ESTATE, "list differs from the evaluation, or a particle is not due at the block time");
     // 3 lanes per particle, units of 10 particles per warp, 4 warps per CTA
     const int cgrid = (int)std::min<int64_t>(((m + 9) / 10 + 3) / 4, 2 * (int64_t)c->num_sms);
-    HG_CUDA(c, launch_correct(c->st, c->d_idx, nullptr, m, c->n, c->ra, c->rj, c->rs, step_params(c), c->d_sc, 0,
-                              cgrid, c->stream));
+    HG_CUDA(c, launch_correct(c->st, c->d_idx, nullptr, m, c->n, c->ra, c->rj, c->rs, c->mixed ? c->rn : nullptr,
+                              step_params(c), c->d_sc, 0, cgrid, c->stream));
     c->tnext_valid = false;
     c->kernels += 1;
     rc = upload_scalar(c, &c->d_sc->t_cur, c->eval_t);

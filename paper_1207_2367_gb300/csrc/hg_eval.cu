@@ -8,8 +8,11 @@
 // tiles filled by 1-D bulk (TMA) copies completing on mbarriers; tpi threads
 // share an i-particle and stride through each tile, then combine with warp
 // shuffles (and shared memory for tpi > 32).  Partial sums of each j-chunk go
-// to a [b][m][9] buffer that the reduction kernel sums in chunk order, so
-// results do not depend on scheduling.
+// to a [b][m][kOut] buffer that the reduction kernel sums in chunk order, so
+// results do not depend on scheduling.  The mixed kernels also sum the noise
+// scale sum_j m_j / (r_ij^2 + eps^2) >= sum_j |a_ij|: FP32 rounding of the pair
+// terms leaves an error in a_i proportional to it, not to |a_i|, which can be
+// hundreds of times smaller where the pull of the system cancels.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -43,6 +46,7 @@ struct Mixed {
     };
     struct Acc {
         float hi[I][9], lo[I][9];
+        float n[I];   // noise scale (positive terms, plain sums of kFold-term chunks)
     };
     typedef float Eps;
 
@@ -64,6 +68,8 @@ struct Mixed {
         for (int k = 0; k < I; ++k)
 #pragma unroll
             for (int c = 0; c < 9; ++c) a.hi[k][c] = a.lo[k][c] = 0.f;
+#pragma unroll
+        for (int k = 0; k < I; ++k) a.n[k] = 0.f;
     }
 
     __device__ static void load(const Records &rec, const int (&ids)[I], ITile &t)
@@ -88,10 +94,11 @@ struct Mixed {
     // A = m r / r^3, J = m v / r^3 - 3 alpha A, S = m a / r^3 - 6 alpha J - 3 beta A,
     // written as A = q r, J = q w, S = q u with q = m / r^3, w = v - 3 alpha r and
     // u = a - 6 alpha w - 3 beta r, so that each sum takes one FMA per component.
+    // ns gathers m / (r^2 + eps^2) >= |A| of every pair but the particle's own.
     template <bool GUARD>
     __device__ __forceinline__ static void pair(const IData &d, const float4 p0, const float4 p1,
                                                 const float4 p2, const float az, const float eps2,
-                                                float (&s)[9])
+                                                float (&s)[9], float &ns)
     {
         const float dx = (p0.x - d.xh) + (p1.x - d.xl);
         const float dy = (p0.y - d.yh) + (p1.y - d.yl);
@@ -104,7 +111,9 @@ struct Mixed {
         rinv = fmaf(0.5f * rinv, fmaf(-r2 * rinv, rinv, 1.f), rinv);
         if (GUARD) rinv = (r2 > 0.f) ? rinv : 0.f;
         const float rinv2 = rinv * rinv;
-        const float q = p0.w * rinv * rinv2;
+        const float mr2 = p0.w * rinv2;
+        const float q = mr2 * rinv;
+        if (r2 != eps2) ns += mr2;   // not the pair with itself (r = 0 exactly; it has no force)
         const float rv = fmaf(dz, dvz, fmaf(dy, dvy, dx * dvx));
         const float v2ra =
             fmaf(dz, daz, fmaf(dy, day, fmaf(dx, dax, fmaf(dvz, dvz, fmaf(dvy, dvy, dvx * dvx)))));
@@ -144,23 +153,27 @@ struct Mixed {
         const int jpt = TJ / tpi;
         const int fold = jpt < kFold ? jpt : kFold;
         for (int g = 0; g < jpt; g += fold) {
-            float ch[I][9];
+            float ch[I][9], cn[I];
 #pragma unroll
-            for (int k = 0; k < I; ++k)
+            for (int k = 0; k < I; ++k) {
+                cn[k] = 0.f;
 #pragma unroll
                 for (int c = 0; c < 9; ++c) ch[k][c] = 0.f;
+            }
 #pragma unroll 2
             for (int u = 0; u < fold; ++u) {
                 const int jj = (g + u) * tpi + lane_j;
                 const float4 p0 = r0[jj], p1 = r1[jj], p2 = r2[jj];
                 const float az = r3[jj];
 #pragma unroll
-                for (int k = 0; k < I; ++k) pair<GUARD>(iv.d[k], p0, p1, p2, az, eps2, ch[k]);
+                for (int k = 0; k < I; ++k) pair<GUARD>(iv.d[k], p0, p1, p2, az, eps2, ch[k], cn[k]);
             }
 #pragma unroll
-            for (int k = 0; k < I; ++k)
+            for (int k = 0; k < I; ++k) {
+                acc.n[k] += cn[k];
 #pragma unroll
                 for (int c = 0; c < 9; ++c) kahan(acc.hi[k][c], acc.lo[k][c], ch[k][c]);
+            }
         }
     }
 
@@ -180,45 +193,54 @@ struct Mixed {
     // (lane_j == 0) hold out = hi - lo in FP64.  On GB300 an FP64 warp
     // instruction costs ~64 cycles, so the tree stays in FP32 and the widening
     // uses the integer f2d.
-    __device__ static void epilogue(Acc &a, int tpi, int tid, double *red, double (&out)[I][9])
+    __device__ static void epilogue(Acc &a, int tpi, int tid, double *red, double (&out)[I][kOut])
     {
         const int wspan = tpi < 32 ? tpi : 32;
         for (int off = 1; off < wspan; off <<= 1) {
 #pragma unroll
-            for (int k = 0; k < I; ++k)
+            for (int k = 0; k < I; ++k) {
 #pragma unroll
                 for (int c = 0; c < 9; ++c) {
                     const float h2 = __shfl_xor_sync(0xffffffffu, a.hi[k][c], off);
                     const float l2 = __shfl_xor_sync(0xffffffffu, a.lo[k][c], off);
                     add_pair(a.hi[k][c], a.lo[k][c], h2, l2);
                 }
+                a.n[k] += __shfl_xor_sync(0xffffffffu, a.n[k], off);
+            }
         }
         if (tpi > 32) {
             float2 *r2 = reinterpret_cast<float2 *>(red);
             const int warp = tid >> 5, lane = tid & 31, wpg = tpi >> 5;
             if (lane == 0) {
 #pragma unroll
-                for (int k = 0; k < I; ++k)
+                for (int k = 0; k < I; ++k) {
 #pragma unroll
-                    for (int c = 0; c < 9; ++c) r2[(warp * I + k) * 9 + c] = make_float2(a.hi[k][c], a.lo[k][c]);
+                    for (int c = 0; c < 9; ++c)
+                        r2[(warp * I + k) * kOut + c] = make_float2(a.hi[k][c], a.lo[k][c]);
+                    r2[(warp * I + k) * kOut + 9] = make_float2(a.n[k], 0.f);
+                }
             }
             __syncthreads();
             if (lane == 0 && (warp % wpg) == 0) {
 #pragma unroll
-                for (int k = 0; k < I; ++k)
+                for (int k = 0; k < I; ++k) {
 #pragma unroll
                     for (int c = 0; c < 9; ++c)
                         for (int g = 1; g < wpg; ++g) {
-                            const float2 v = r2[((warp + g) * I + k) * 9 + c];
+                            const float2 v = r2[((warp + g) * I + k) * kOut + c];
                             add_pair(a.hi[k][c], a.lo[k][c], v.x, v.y);
                         }
+                    for (int g = 1; g < wpg; ++g) a.n[k] += r2[((warp + g) * I + k) * kOut + 9].x;
+                }
             }
             __syncthreads();
         }
 #pragma unroll
-        for (int k = 0; k < I; ++k)
+        for (int k = 0; k < I; ++k) {
 #pragma unroll
             for (int c = 0; c < 9; ++c) out[k][c] = f2d(a.hi[k][c]) - f2d(a.lo[k][c]);
+            out[k][9] = f2d(a.n[k]);
+        }
     }
 };
 
@@ -326,13 +348,16 @@ struct F64 {
     }
 
     // Sum the tpi lanes sharing an i-particle (fixed xor tree; shared memory
-    // across warps for tpi = 64): the leader lanes (lane_j == 0) hold out.
-    __device__ static void epilogue(Acc &a, int tpi, int tid, double *red, double (&out)[I][9])
+    // across warps for tpi = 64): the leader lanes (lane_j == 0) hold out.  No
+    // noise scale (out[k][9] = 0): the FP64 path needs no noise floor.
+    __device__ static void epilogue(Acc &a, int tpi, int tid, double *red, double (&out)[I][kOut])
     {
 #pragma unroll
-        for (int k = 0; k < I; ++k)
+        for (int k = 0; k < I; ++k) {
 #pragma unroll
             for (int c = 0; c < 9; ++c) out[k][c] = a.s[k][c];
+            out[k][9] = 0.0;
+        }
         const int wspan = tpi < 32 ? tpi : 32;
         for (int off = 1; off < wspan; off <<= 1) {
 #pragma unroll
@@ -346,7 +371,7 @@ struct F64 {
 #pragma unroll
                 for (int k = 0; k < I; ++k)
 #pragma unroll
-                    for (int c = 0; c < 9; ++c) red[(warp * I + k) * 9 + c] = out[k][c];
+                    for (int c = 0; c < 9; ++c) red[(warp * I + k) * kOut + c] = out[k][c];
             }
             __syncthreads();
             if (lane == 0 && (warp % wpg) == 0) {
@@ -354,8 +379,8 @@ struct F64 {
                 for (int k = 0; k < I; ++k)
 #pragma unroll
                     for (int c = 0; c < 9; ++c) {
-                        double s = red[(warp * I + k) * 9 + c];
-                        for (int g = 1; g < wpg; ++g) s += red[((warp + g) * I + k) * 9 + c];
+                        double s = red[(warp * I + k) * kOut + c];
+                        for (int g = 1; g < wpg; ++g) s += red[((warp + g) * I + k) * kOut + c];
                         out[k][c] = s;
                     }
             }
@@ -371,7 +396,7 @@ template <class P>
 constexpr size_t smem_bytes()
 {
     return (size_t)kStages * P::kStageBytes + kStages * sizeof(uint64_t) +
-           (kEvalThreads / 32) * P::I * 9 * sizeof(double);
+           (kEvalThreads / 32) * P::I * kOut * sizeof(double);
 }
 
 template <class P, bool GUARD>
@@ -485,18 +510,20 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
         }
         seq += (uint32_t)nt;
 
-        double out[P::I][9];
+        double out[P::I][kOut];
         P::epilogue(acc, tpi, tid, red, out);
         if (!batch && args.direct_b1 && pl.b == 1) {   // no j-split: these are the results
             if (lane_j == 0) {
 #pragma unroll
                 for (int k = 0; k < P::I; ++k)
-                    if (qi[k] < q_end)
+                    if (qi[k] < q_end) {
 #pragma unroll
                         for (int c = 0; c < 9; ++c) {
                             double *dst = c < 3 ? args.ra : (c < 6 ? args.rj : args.rs);
                             dst[qi[k] * 3 + c % 3] = out[k][c];
                         }
+                        if (args.rn) args.rn[qi[k]] = out[k][9];
+                    }
             }
             continue;
         }
@@ -504,9 +531,9 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
 #pragma unroll
             for (int k = 0; k < P::I; ++k) {
                 if (qi[k] < q_end) {
-                    double *dst = args.partial + (rbase + qi[k]) * 9;
+                    double *dst = args.partial + (rbase + qi[k]) * kOut;
 #pragma unroll
-                    for (int c = 0; c < 9; ++c) dst[c] = out[k][c];
+                    for (int c = 0; c < kOut; ++c) dst[c] = out[k][c];
                 }
             }
         }
@@ -514,59 +541,66 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
 }
 
 // Table 1 section 4: sum the b j-chunk partials of every listed particle in
-// chunk order and scatter them to acc/jerk/snap [m][3].
+// chunk order and scatter them to acc/jerk/snap [m][3] (and the noise scale to
+// args.rn [m] when it is set).
+__device__ __forceinline__ void put_result(const EvalArgs &a, double *ra, double *rj, double *rs, int64_t q, int c,
+                                           double v)
+{
+    if (c == 9) {
+        if (a.rn) a.rn[q] = v;
+        return;
+    }
+    double *dst = c < 3 ? ra : (c < 6 ? rj : rs);
+    dst[q * 3 + (c % 3)] = v;
+}
+
 __global__ void k_reduce(const EvalArgs args, double *ra, double *rj, double *rs)
 {
     const int64_t m = args.m_dev ? *args.m_dev : args.m_host;
     if (m <= 0) return;
     const Plan pl = args.plan_dev ? *args.plan_dev : args.plan_host;
     if (args.bv.nc == 0 && args.direct_b1 && pl.b == 1) return;   // the evaluation wrote the results
-    const int64_t total = m * 9;
+    const int64_t total = m * kOut;
     if (args.bv.nc > 0) {
         // Clusters: the chunks of position q are rows part_off[c] + s * m_c + (q - a_off[c]).
         const BatchView &bv = args.bv;
         for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
              e += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t q = e / 9;
-            const int c9 = (int)(e - q * 9);
+            const int64_t q = e / kOut;
+            const int cv = (int)(e - q * kOut);
             const int c = bv.cl_of[args.idx[q]];
             const int64_t qb = bv.a_off[c], mc = bv.a_off[c + 1] - qb;
             const int64_t row0 = bv.part_off[c] + (q - qb);
             const int b = bv.b_c[c];
             double s = 0.0;
-            for (int sp = 0; sp < b; ++sp) s += args.partial[(row0 + (int64_t)sp * mc) * 9 + c9];
-            double *dst = c9 < 3 ? ra : (c9 < 6 ? rj : rs);
-            dst[q * 3 + (c9 % 3)] = s;
+            for (int sp = 0; sp < b; ++sp) s += args.partial[(row0 + (int64_t)sp * mc) * kOut + cv];
+            put_result(args, ra, rj, rs, q, cv, s);
         }
         return;
     }
     if (pl.b <= 32) {
-        // Few chunks: one thread per (particle, component), chunks in order.
+        // Few chunks: one thread per (particle, value), chunks in order.
         for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
              e += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t q = e / 9;
-            const int c = (int)(e - q * 9);
+            const int64_t q = e / kOut;
+            const int c = (int)(e - q * kOut);
             double s = 0.0;
-            for (int sp = 0; sp < pl.b; ++sp) s += args.partial[((int64_t)sp * m + q) * 9 + c];
-            double *dst = c < 3 ? ra : (c < 6 ? rj : rs);
-            dst[q * 3 + (c % 3)] = s;
+            for (int sp = 0; sp < pl.b; ++sp) s += args.partial[((int64_t)sp * m + q) * kOut + c];
+            put_result(args, ra, rj, rs, q, c, s);
         }
     } else {
-        // Many chunks (small blocks): one warp per (particle, component); lane l
+        // Many chunks (small blocks): one warp per (particle, value); lane l
         // sums chunks l, l+32, ..., then a fixed butterfly combines the lanes.
         const int lane = threadIdx.x & 31;
         const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
         const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
         for (int64_t e = wid; e < total; e += nw) {
-            const int64_t q = e / 9;
-            const int c = (int)(e - q * 9);
+            const int64_t q = e / kOut;
+            const int c = (int)(e - q * kOut);
             double s = 0.0;
-            for (int sp = lane; sp < pl.b; sp += 32) s += args.partial[((int64_t)sp * m + q) * 9 + c];
+            for (int sp = lane; sp < pl.b; sp += 32) s += args.partial[((int64_t)sp * m + q) * kOut + c];
             for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            if (lane == 0) {
-                double *dst = c < 3 ? ra : (c < 6 ? rj : rs);
-                dst[q * 3 + (c % 3)] = s;
-            }
+            if (lane == 0) put_result(args, ra, rj, rs, q, c, s);
         }
     }
 }

@@ -218,6 +218,11 @@ __host__ __device__ inline BatchKnobs batch_knobs(int64_t m, const PlanParams &q
     return BatchKnobs{v & 7, (v >> 3) - 1};
 }
 
+// Values per partial-sum row and per evaluated particle: acceleration, jerk and
+// snap (3 each), then the noise scale sum_j m_j / (r_ij^2 + eps^2), an upper
+// bound of sum_j |a_ij| (mixed kernels; the FP64 kernel writes 0).
+constexpr int kOut = 10;
+
 struct EvalArgs {
     Records rec{};
     int64_t npad = 0;
@@ -226,7 +231,7 @@ struct EvalArgs {
     int64_t m_host = 0;                // block size when m_dev == nullptr
     const Plan *plan_dev = nullptr;    // plan on the device (graph mode), or nullptr
     Plan plan_host{};                  // plan when plan_dev == nullptr
-    double *partial = nullptr;         // [b][m][9] partial sums
+    double *partial = nullptr;         // [b][m][kOut] partial sums
     double eps2 = 0.0;
     int guard = 0;                     // eps == 0: skip r^2 == 0 pairs
     uint32_t tx_extra = 0;             // testing: bytes expected per tile beyond those copied (0 normally)
@@ -234,9 +239,10 @@ struct EvalArgs {
     BatchView bv{};                    // clusters (bv.nc == 0: single system)
     // One system: a plan without j-split (b = 1) writes its sums straight into
     // ra/rj/rs [m][3] and the reduction kernel returns at once (direct_b1 = 1);
-    // otherwise partials go to [b][m][9] and the reduction kernel sums them.
+    // otherwise partials go to [b][m][kOut] and the reduction kernel sums them.
     int direct_b1 = 0;
     double *ra = nullptr, *rj = nullptr, *rs = nullptr;
+    double *rn = nullptr;              // [m] noise scale (nullptr: not written)
 };
 
 // Planner inputs of one precision (hg_eval.cu): tiles, tile size, i per thread,
@@ -256,8 +262,9 @@ int eval_grid(bool mixed, int num_sms);
 cudaError_t launch_eval(bool mixed, const EvalArgs &args, int num_sms, cudaStream_t st);
 // Kernels launch_eval issues for a device plan.
 int eval_launches(bool mixed, const EvalArgs &args);
-// Sums the b partials of each listed particle into res_{a,j,s} [m][3]
-// (grid-stride: grid CTAs of 256 threads, a few per SM).
+// Sums the b partials of each listed particle into res_{a,j,s} [m][3] and, when
+// args.rn is set, the noise scale into args.rn [m] (grid-stride: grid CTAs of
+// 256 threads, a few per SM).
 cudaError_t launch_reduce(const EvalArgs &args, double *ra, double *rj, double *rs, int grid, cudaStream_t st);
 
 // ---------------------------------------------------------------------------

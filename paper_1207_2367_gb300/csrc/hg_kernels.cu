@@ -698,16 +698,18 @@ __device__ __forceinline__ bool multiple_of_pow2(double t1, int p)
 __device__ __forceinline__ double sq3(const double *p) { return p[0] * p[0] + p[1] * p[1] + p[2] * p[2]; }
 
 // New time and p = 6 step of particle i from d = a^(0..5) at the step's end.
-// A: the acceleration change left after a0 + j0 h + s0 h^2/2.  Below the noise
-// floor of the evaluation (sp.noise_rel |a1|, compared as squares) the
-// interpolated derivatives are noise and the criterion may not shrink the step.
+// A: the acceleration change left after a0 + j0 h + s0 h^2/2 (a0 + j0 h for
+// p = 4).  Below the noise floor of the evaluation, sp.noise_rel times the
+// noise scale (sum_j m_j / r_ij^2 where the evaluation provides it, else |a1|;
+// compared as squares), the interpolated derivatives are noise and the
+// criterion may not shrink the step.
 template <int P>
 __device__ __forceinline__ double finish_step(const State &st, int64_t i, double h, int e, bool pow2,
-                                              const double (*d)[3], const double *A, const StepParams &sp,
-                                              bool store)
+                                              const double (*d)[3], const double *A, double scale2,
+                                              const StepParams &sp, bool store)
 {
     const double t1 = st.t[i] + h;
-    const bool noisy = sp.noise_rel > 0.0 && sq3(A) < (sp.noise_rel * sp.noise_rel) * sq3(d[0]);
+    const bool noisy = sp.noise_rel > 0.0 && sq3(A) < (sp.noise_rel * sp.noise_rel) * scale2;
     double dt1;
     int F, kmin, kmax;
     double qn[P];
@@ -749,8 +751,8 @@ constexpr int kCorrUnit = 10;
 
 template <int P>
 __device__ __forceinline__ void correct_lane(const State &st, const int32_t *idx, const double *ra, const double *rj,
-                                             const double *rs, const StepParams &sp, int64_t m, int64_t u,
-                                             long long &low)
+                                             const double *rs, const double *rn, const StepParams &sp, int64_t m,
+                                             int64_t u, long long &low)
 {
     const int lane = threadIdx.x & 31, sub = lane / 3, k = lane - 3 * sub;
     const int64_t q = u * kCorrUnit + sub;
@@ -781,12 +783,16 @@ __device__ __forceinline__ void correct_lane(const State &st, const int32_t *idx
         for (int r = 0; r < P; ++r) d[r][c] = __shfl_sync(0xffffffffu, dk[r], src);
         A[c] = __shfl_sync(0xffffffffu, Ak, src);
     }
-    if (act) low = min(low, __double_as_longlong(finish_step<P>(st, i, h, e, pow2, d, A, sp, k == 0)));
+    if (act) {
+        const double scale2 = rn ? rn[q] * rn[q] : sq3(d[0]);
+        low = min(low, __double_as_longlong(finish_step<P>(st, i, h, e, pow2, d, A, scale2, sp, k == 0)));
+    }
 }
 
 __global__ void __launch_bounds__(128) k_correct(State st, const int32_t *idx, const int64_t *m_dev, int64_t m_host,
-                                                 const double *ra, const double *rj, const double *rs, StepParams sp,
-                                                 DevScalars *sc, int64_t n, int min_pass)
+                                                 const double *ra, const double *rj, const double *rs,
+                                                 const double *rn, StepParams sp, DevScalars *sc, int64_t n,
+                                                 int min_pass)
 {
     __shared__ long long sh[32];
     const int64_t m = m_dev ? *m_dev : m_host;
@@ -796,9 +802,9 @@ __global__ void __launch_bounds__(128) k_correct(State st, const int32_t *idx, c
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units; u += nw) {   // warp-uniform
         if (sp.order == 4)
-            correct_lane<4>(st, idx, ra, rj, rs, sp, m, u, low);
+            correct_lane<4>(st, idx, ra, rj, rs, rn, sp, m, u, low);
         else
-            correct_lane<6>(st, idx, ra, rj, rs, sp, m, u, low);
+            correct_lane<6>(st, idx, ra, rj, rs, rn, sp, m, u, low);
     }
     if (!min_pass) return;
     // Next block time: min over the new tend of the particles corrected here and
@@ -1335,10 +1341,10 @@ cudaError_t launch_start(const State &st, int64_t n, const double *ra, const dou
 }
 
 cudaError_t launch_correct(const State &st, const int32_t *idx, const int64_t *m_dev, int64_t m_host, int64_t n,
-                           const double *ra, const double *rj, const double *rs, const StepParams &sp,
-                           DevScalars *sc, int min_pass, int grid, cudaStream_t s)
+                           const double *ra, const double *rj, const double *rs, const double *rn,
+                           const StepParams &sp, DevScalars *sc, int min_pass, int grid, cudaStream_t s)
 {
-    k_correct<<<grid, 128, 0, s>>>(st, idx, m_dev, m_host, ra, rj, rs, sp, sc, n, min_pass);
+    k_correct<<<grid, 128, 0, s>>>(st, idx, m_dev, m_host, ra, rj, rs, rn, sp, sc, n, min_pass);
     return cudaGetLastError();
 }
 

@@ -8,8 +8,9 @@ namespace hg {
 struct StepParams {
     double eta, eta_init, dt_min, dt_max;
     // Relative noise floor of the evaluated acceleration (0: exact enough, FP64).
-    // When |a1 - a0 - j0 h - s0 h^2/2| < noise_rel |a1| the interpolated crackle,
-    // pop and 5th derivative are unresolved: the criterion then does not shrink the step.
+    // When |a1 - a0 - j0 h - s0 h^2/2| < noise_rel * scale (the evaluation's
+    // noise scale sum_j m_j / r_ij^2, else |a1|) the interpolated crackle, pop
+    // and 5th derivative are unresolved: the criterion then does not shrink the step.
     double noise_rel;
     float log2_eta;   // log2(eta), for the FP32 estimate of the criterion
     int order;        // 6: the paper's scheme (p = 6); 4: the 4th-order scheme (p = 4)
@@ -51,10 +52,11 @@ cudaError_t launch_start(const State &st, int64_t n, const double *ra, const dou
 // Corrector and new steps of the listed particles.  min_pass (graph steps of
 // one system, where the list is every particle due at sc->t_cur): also leave
 // min_i tend_i of the new state in sc->tnext_bits (reset beforehand by the
-// selection).  grid: CTAs of 128 threads.
+// selection).  rn: noise scale of each listed particle (mixed), or nullptr
+// (the noise floor then scales with |a1|).  grid: CTAs of 128 threads.
 cudaError_t launch_correct(const State &st, const int32_t *idx, const int64_t *m_dev, int64_t m_host, int64_t n,
-                           const double *ra, const double *rj, const double *rs, const StepParams &sp,
-                           DevScalars *sc, int min_pass, int grid, cudaStream_t s);
+                           const double *ra, const double *rj, const double *rs, const double *rn,
+                           const StepParams &sp, DevScalars *sc, int min_pass, int grid, cudaStream_t s);
 int energy_splits(int64_t n, int num_sms);
 cudaError_t launch_energy(bool mixed, const State &st, int64_t n, double t, double eps2, double *xe, double *ve,
                           double *phi_part, int nsplit, double *part2, int g2, double *out2, const BatchView &bv,

@@ -21,7 +21,7 @@ namespace {
 constexpr int64_t kStaticMaxN = 16384;                    // particles (multiple of the j-tiles)
 constexpr size_t kRecBytes = 5 * (size_t)kStaticMaxN * 16;   // largest record layout (fp64: 80 B)
 constexpr int64_t kStaticPcap = 4 * kStaticMaxN;            // partial sums: b * m <= kStaticPcap
-constexpr size_t kPartBytes = (size_t)kStaticPcap * 9 * sizeof(double);
+constexpr size_t kPartBytes = (size_t)kStaticPcap * kOut * sizeof(double);
 constexpr size_t kFlagBytes = 256;                          // int32 error word, int32 check flag
 constexpr size_t kScratchBytes = kRecBytes + kPartBytes + kFlagBytes;
 constexpr int kMaxDevices = 64;
