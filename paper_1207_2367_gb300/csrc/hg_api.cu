@@ -398,12 +398,10 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
     bool ok = alloc_state(c, c->st) && alloc_state(c, c->st2);
     c->own = c->st;
     if (c->mixed) {
-        c->rec.p[0] = dalloc<float4>(c, c->npad);
-        c->rec.p[1] = dalloc<float4>(c, c->npad);
-        c->rec.p[2] = dalloc<float4>(c, c->npad);
-        c->rec.p[3] = dalloc<float>(c, c->npad);
-        c->rec.p[4] = nullptr;
-        ok = ok && c->rec.p[0] && c->rec.p[1] && c->rec.p[2] && c->rec.p[3];
+        for (int q = 0; q < kMixedArrays; ++q) {   // record pairs: six float4 arrays and one float2
+            c->rec.p[q] = q < 6 ? (void *)dalloc<float4>(c, c->npad / 2) : (void *)dalloc<float2>(c, c->npad / 2);
+            ok = ok && c->rec.p[q];
+        }
     } else {
         for (int q = 0; q < 5; ++q) {
             c->rec.p[q] = dalloc<double2>(c, c->npad);

@@ -27,22 +27,28 @@ constexpr int kFold = 32;   // FP32 pair sums are folded into the compensated su
 // Mixed precision: FP32 pair arithmetic, double-single position differences,
 // Kahan-compensated FP32 sums (Sect. 5.7 hybrid precision, redesigned).
 // ------------------------------------------------------------------------
-// IPT i-particles per thread: 2 with 4 CTAs per SM (128 registers) for small
-// and medium blocks, 3 with 2 CTAs per SM for large ones (more independent
-// pair chains per warp and fewer shared-memory loads per pair; ~9 % more pairs
-// per second at m = N, but a longer latency for small blocks).
+// Each lane takes the j-records two at a time (one pair of the interleaved
+// layout) and evaluates both pairs (i, 2P) and (i, 2P+1) with packed f32x2
+// operations: the halves of every register pair belong to the two j, the
+// i-particle's values are duplicated into both halves once per work item.
+// One packed instruction does the FP32 work of two, so the issue slots per
+// pair interaction halve and the FP32 pipe (not instruction issue) becomes
+// the limit.  IPT i-particles per thread: 1 for small and medium blocks
+// (short latency, more CTAs per SM), 2 for large ones.
 template <int IPT>
 struct Mixed {
     static constexpr int TJ = kTJMixed;
+    static constexpr int TP = TJ / 2;   // record pairs per tile
     static constexpr int I = IPT;
-    static constexpr int kMinBlocks = IPT == kIMixed ? 4 : 2;
+    static constexpr int kMinBlocks = IPT == kIMixed ? 3 : 2;
     static constexpr int kVariant = IPT == kIMixed ? 0 : 1;
     static constexpr uint32_t kStageBytes = TJ * 52;
     struct IData {
-        float xh, yh, zh, xl, yl, zl, vx, vy, vz, ax, ay, az;
+        f2_t xh, yh, zh, xl, yl, zl, vx, vy, vz, ax, ay, az;   // (v, v) duplicated
     };
     struct ITile {
         IData d[I];
+        int rid[I];   // record index of each i-particle (its own pair is left out of the noise scale)
     };
     struct Acc {
         float hi[I][9], lo[I][9];
@@ -50,87 +56,100 @@ struct Mixed {
     };
     typedef float Eps;
 
-    __device__ static void load_i(const Records &rec, int i, IData &d)
+    __device__ static void load_i(const Records &rec, int r, IData &d)
     {
-        const float4 p0 = __ldg(static_cast<const float4 *>(rec.p[0]) + i);
-        const float4 p1 = __ldg(static_cast<const float4 *>(rec.p[1]) + i);
-        const float4 p2 = __ldg(static_cast<const float4 *>(rec.p[2]) + i);
-        const float p3 = __ldg(static_cast<const float *>(rec.p[3]) + i);
-        d.xh = p0.x; d.yh = p0.y; d.zh = p0.z;
-        d.xl = p1.x; d.yl = p1.y; d.zl = p1.z; d.ax = p1.w;
-        d.vx = p2.x; d.vy = p2.y; d.vz = p2.z; d.ay = p2.w;
-        d.az = p3;
+        const MixedRecord v = load_mixed_record(rec, r);
+        d.xh = f2_pack(v.xh, v.xh); d.yh = f2_pack(v.yh, v.yh); d.zh = f2_pack(v.zh, v.zh);
+        d.xl = f2_pack(v.xl, v.xl); d.yl = f2_pack(v.yl, v.yl); d.zl = f2_pack(v.zl, v.zl);
+        d.vx = f2_pack(v.vx, v.vx); d.vy = f2_pack(v.vy, v.vy); d.vz = f2_pack(v.vz, v.vz);
+        d.ax = f2_pack(v.ax, v.ax); d.ay = f2_pack(v.ay, v.ay); d.az = f2_pack(v.az, v.az);
     }
 
     __device__ static void zero(Acc &a)
     {
 #pragma unroll
-        for (int k = 0; k < I; ++k)
+        for (int k = 0; k < I; ++k) {
+            a.n[k] = 0.f;
 #pragma unroll
             for (int c = 0; c < 9; ++c) a.hi[k][c] = a.lo[k][c] = 0.f;
-#pragma unroll
-        for (int k = 0; k < I; ++k) a.n[k] = 0.f;
+        }
     }
 
     __device__ static void load(const Records &rec, const int (&ids)[I], ITile &t)
     {
 #pragma unroll
-        for (int k = 0; k < I; ++k) load_i(rec, ids[k], t.d[k]);
+        for (int k = 0; k < I; ++k) {
+            load_i(rec, ids[k], t.d[k]);
+            t.rid[k] = ids[k];
+        }
     }
 
     __device__ static void issue(const Records &rec, int64_t tile, unsigned char *dst, uint64_t *bar,
                                  uint32_t tx_extra)
     {
-        const int64_t j0 = tile * TJ;
+        const int64_t p0 = tile * TP;
         mbar_arrive_expect_tx(bar, kStageBytes + tx_extra);
-        bulk_g2s(dst, static_cast<const float4 *>(rec.p[0]) + j0, TJ * 16, bar);
-        bulk_g2s(dst + TJ * 16, static_cast<const float4 *>(rec.p[1]) + j0, TJ * 16, bar);
-        bulk_g2s(dst + TJ * 32, static_cast<const float4 *>(rec.p[2]) + j0, TJ * 16, bar);
-        bulk_g2s(dst + TJ * 48, static_cast<const float *>(rec.p[3]) + j0, TJ * 4, bar);
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+            bulk_g2s(dst + q * TP * 16, static_cast<const float4 *>(rec.p[q]) + p0, TP * 16, bar);
+        bulk_g2s(dst + 6 * TP * 16, static_cast<const float2 *>(rec.p[6]) + p0, TP * 8, bar);
     }
 
-    // One pair: r_ij = r_j - r_i from (hi, lo) parts, v_ij, a_ij, softened r^2,
-    // alpha r^2 = r.v, beta r^2 = v^2 + r.a + alpha^2 r^2, and
+    // Pairs (i, 2P) and (i, 2P+1): r_ij = r_j - r_i from (hi, lo) parts, v_ij,
+    // a_ij, softened r^2, alpha r^2 = r.v, beta r^2 = v^2 + r.a + alpha^2 r^2, and
     // A = m r / r^3, J = m v / r^3 - 3 alpha A, S = m a / r^3 - 6 alpha J - 3 beta A,
     // written as A = q r, J = q w, S = q u with q = m / r^3, w = v - 3 alpha r and
     // u = a - 6 alpha w - 3 beta r, so that each sum takes one FMA per component.
-    // ns gathers m / (r^2 + eps^2) >= |A| of every pair but the particle's own.
+    // ns gathers m / (r^2 + eps^2) (>= |A|) times keep: (1, 1), or 0 in the half
+    // holding the i-particle itself.
     template <bool GUARD>
-    __device__ __forceinline__ static void pair(const IData &d, const float4 p0, const float4 p1,
-                                                const float4 p2, const float az, const float eps2,
-                                                float (&s)[9], float &ns)
+    __device__ __forceinline__ static void pair(const IData &d, const float4 q0, const float4 q1,
+                                                const float4 q2, const float4 q3, const float4 q4,
+                                                const float4 q5, const float2 q6, const f2_t eps2, f2_t keep,
+                                                f2_t (&s)[9], f2_t &ns)
     {
-        const float dx = (p0.x - d.xh) + (p1.x - d.xl);
-        const float dy = (p0.y - d.yh) + (p1.y - d.yl);
-        const float dz = (p0.z - d.zh) + (p1.z - d.zl);
-        const float dvx = p2.x - d.vx, dvy = p2.y - d.vy, dvz = p2.z - d.vz;
-        const float dax = p1.w - d.ax, day = p2.w - d.ay, daz = az - d.az;
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-        float rinv = rsqrt_approx(r2);
-        // One Newton-Raphson step for 1/sqrt(r2): y <- y + y/2 (1 - r2 y^2).
-        rinv = fmaf(0.5f * rinv, fmaf(-r2 * rinv, rinv, 1.f), rinv);
-        if (GUARD) rinv = (r2 > 0.f) ? rinv : 0.f;
-        const float rinv2 = rinv * rinv;
-        const float mr2 = p0.w * rinv2;
-        const float q = mr2 * rinv;
-        if (r2 != eps2) ns += mr2;   // not the pair with itself (r = 0 exactly; it has no force)
-        const float rv = fmaf(dz, dvz, fmaf(dy, dvy, dx * dvx));
-        const float v2ra =
-            fmaf(dz, daz, fmaf(dy, day, fmaf(dx, dax, fmaf(dvz, dvz, fmaf(dvy, dvy, dvx * dvx)))));
-        const float alpha = rv * rinv2;
-        const float beta = fmaf(alpha, alpha, v2ra * rinv2);
-        const float a3 = -3.f * alpha;
-        const float a6 = a3 + a3, b3 = -3.f * beta;
-        const float wx = fmaf(a3, dx, dvx), wy = fmaf(a3, dy, dvy), wz = fmaf(a3, dz, dvz);
-        s[0] = fmaf(q, dx, s[0]);
-        s[1] = fmaf(q, dy, s[1]);
-        s[2] = fmaf(q, dz, s[2]);
-        s[3] = fmaf(q, wx, s[3]);
-        s[4] = fmaf(q, wy, s[4]);
-        s[5] = fmaf(q, wz, s[5]);
-        s[6] = fmaf(q, fmaf(b3, dx, fmaf(a6, wx, dax)), s[6]);
-        s[7] = fmaf(q, fmaf(b3, dy, fmaf(a6, wy, day)), s[7]);
-        s[8] = fmaf(q, fmaf(b3, dz, fmaf(a6, wz, daz)), s[8]);
+        const f2_t k_nhalf = f2_pack(-0.5f, -0.5f), k_half = f2_pack(0.5f, 0.5f), k_m3 = f2_pack(-3.f, -3.f);
+        const f2_t dx = f2_add(f2_sub(f2_pack(q0.x, q0.y), d.xh), f2_sub(f2_pack(q2.x, q2.y), d.xl));
+        const f2_t dy = f2_add(f2_sub(f2_pack(q0.z, q0.w), d.yh), f2_sub(f2_pack(q2.z, q2.w), d.yl));
+        const f2_t dz = f2_add(f2_sub(f2_pack(q1.x, q1.y), d.zh), f2_sub(f2_pack(q3.x, q3.y), d.zl));
+        const f2_t dvx = f2_sub(f2_pack(q4.x, q4.y), d.vx);
+        const f2_t dvy = f2_sub(f2_pack(q4.z, q4.w), d.vy);
+        const f2_t dvz = f2_sub(f2_pack(q5.x, q5.y), d.vz);
+        const f2_t dax = f2_sub(f2_pack(q3.z, q3.w), d.ax);
+        const f2_t day = f2_sub(f2_pack(q5.z, q5.w), d.ay);
+        const f2_t daz = f2_sub(f2_pack(q6.x, q6.y), d.az);
+        const f2_t r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_fma(dx, dx, eps2)));
+        const float2 r2s = f2_unpack(r2);
+        float y0 = rsqrt_approx(r2s.x), y1 = rsqrt_approx(r2s.y);
+        if (GUARD) {
+            y0 = r2s.x > 0.f ? y0 : 0.f;
+            y1 = r2s.y > 0.f ? y1 : 0.f;
+        }
+        // One Newton-Raphson step for 1/sqrt(r2): y <- y + y (1/2 - r2 y^2 / 2).
+        f2_t y = f2_pack(y0, y1);
+        const f2_t e = f2_fma(f2_mul(f2_mul(r2, k_nhalf), y), y, k_half);
+        y = f2_fma(y, e, y);
+        const f2_t rinv2 = f2_mul(y, y);
+        const f2_t mr2 = f2_mul(f2_pack(q1.z, q1.w), rinv2);
+        const f2_t q = f2_mul(mr2, y);
+        ns = f2_fma(mr2, keep, ns);
+        const f2_t rv = f2_fma(dz, dvz, f2_fma(dy, dvy, f2_mul(dx, dvx)));
+        const f2_t v2ra =
+            f2_fma(dz, daz, f2_fma(dy, day, f2_fma(dx, dax, f2_fma(dvz, dvz, f2_fma(dvy, dvy, f2_mul(dvx, dvx))))));
+        const f2_t alpha = f2_mul(rv, rinv2);
+        const f2_t beta = f2_fma(alpha, alpha, f2_mul(v2ra, rinv2));
+        const f2_t a3 = f2_mul(k_m3, alpha);
+        const f2_t a6 = f2_add(a3, a3), b3 = f2_mul(k_m3, beta);
+        const f2_t wx = f2_fma(a3, dx, dvx), wy = f2_fma(a3, dy, dvy), wz = f2_fma(a3, dz, dvz);
+        s[0] = f2_fma(q, dx, s[0]);
+        s[1] = f2_fma(q, dy, s[1]);
+        s[2] = f2_fma(q, dz, s[2]);
+        s[3] = f2_fma(q, wx, s[3]);
+        s[4] = f2_fma(q, wy, s[4]);
+        s[5] = f2_fma(q, wz, s[5]);
+        s[6] = f2_fma(q, f2_fma(b3, dx, f2_fma(a6, wx, dax)), s[6]);
+        s[7] = f2_fma(q, f2_fma(b3, dy, f2_fma(a6, wy, day)), s[7]);
+        s[8] = f2_fma(q, f2_fma(b3, dz, f2_fma(a6, wz, daz)), s[8]);
     }
 
     // Kahan step: hi + x with the running compensation lo (true sum = hi - lo).
@@ -142,37 +161,53 @@ struct Mixed {
         hi = t;
     }
 
+    // tile: absolute index of the j-tile, to find the pair holding each
+    // i-particle's own record.
     template <bool GUARD>
     __device__ static void tile(const unsigned char *sb, int tpi, int lane_j, const ITile &iv, Acc &acc,
-                                Eps eps2)
+                                Eps eps2s, int64_t tile)
     {
-        const float4 *r0 = reinterpret_cast<const float4 *>(sb);
-        const float4 *r1 = r0 + TJ;
-        const float4 *r2 = r1 + TJ;
-        const float *r3 = reinterpret_cast<const float *>(r2 + TJ);
-        const int jpt = TJ / tpi;
-        const int fold = jpt < kFold ? jpt : kFold;
-        for (int g = 0; g < jpt; g += fold) {
-            float ch[I][9], cn[I];
+        const float4 *a0 = reinterpret_cast<const float4 *>(sb);
+        const float2 *a6 = reinterpret_cast<const float2 *>(a0 + 6 * TP);
+        const f2_t eps2 = f2_pack(eps2s, eps2s);
+        const f2_t one2 = f2_pack(1.f, 1.f);
+        int selfp[I];   // pair of this tile holding i-particle k's own record, or -1
+        f2_t selfk[I];  // keep-mask of that pair
+#pragma unroll
+        for (int k = 0; k < I; ++k) {
+            const int64_t r = iv.rid[k];
+            selfp[k] = (r / TJ == tile) ? (int)((r % TJ) >> 1) : -1;
+            selfk[k] = (r & 1) ? f2_pack(1.f, 0.f) : f2_pack(0.f, 1.f);
+        }
+        const int ppt = TP / tpi;   // pairs per lane in this tile
+        const int fold = ppt < kFold / 2 ? ppt : kFold / 2;
+        for (int g = 0; g < ppt; g += fold) {
+            f2_t ch[I][9], cn[I];
 #pragma unroll
             for (int k = 0; k < I; ++k) {
-                cn[k] = 0.f;
+                cn[k] = 0ull;
 #pragma unroll
-                for (int c = 0; c < 9; ++c) ch[k][c] = 0.f;
+                for (int c = 0; c < 9; ++c) ch[k][c] = 0ull;
             }
-#pragma unroll 2
             for (int u = 0; u < fold; ++u) {
-                const int jj = (g + u) * tpi + lane_j;
-                const float4 p0 = r0[jj], p1 = r1[jj], p2 = r2[jj];
-                const float az = r3[jj];
+                const int jp = (g + u) * tpi + lane_j;
+                const float4 q0 = a0[jp], q1 = a0[TP + jp], q2 = a0[2 * TP + jp], q3 = a0[3 * TP + jp],
+                             q4 = a0[4 * TP + jp], q5 = a0[5 * TP + jp];
+                const float2 q6 = a6[jp];
 #pragma unroll
-                for (int k = 0; k < I; ++k) pair<GUARD>(iv.d[k], p0, p1, p2, az, eps2, ch[k], cn[k]);
+                for (int k = 0; k < I; ++k)
+                    pair<GUARD>(iv.d[k], q0, q1, q2, q3, q4, q5, q6, eps2, jp == selfp[k] ? selfk[k] : one2,
+                                ch[k], cn[k]);
             }
 #pragma unroll
             for (int k = 0; k < I; ++k) {
-                acc.n[k] += cn[k];
+                const float2 nn = f2_unpack(cn[k]);
+                acc.n[k] += nn.x + nn.y;
 #pragma unroll
-                for (int c = 0; c < 9; ++c) kahan(acc.hi[k][c], acc.lo[k][c], ch[k][c]);
+                for (int c = 0; c < 9; ++c) {
+                    const float2 v = f2_unpack(ch[k][c]);
+                    kahan(acc.hi[k][c], acc.lo[k][c], v.x + v.y);
+                }
             }
         }
     }
@@ -333,7 +368,7 @@ struct F64 {
 
     template <bool GUARD>
     __device__ static void tile(const unsigned char *sb, int tpi, int lane_j, const ITile &iv, Acc &acc,
-                                Eps eps2)
+                                Eps eps2, int64_t)
     {
         const double2 *q0 = reinterpret_cast<const double2 *>(sb);
         const int jpt = TJ / tpi;
@@ -491,7 +526,7 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
             const uint32_t sq = seq + (uint32_t)t;
             const int st = (int)(sq % kStages);
             const bool ok = mbar_wait_bounded(&bars[st], (sq / kStages) & 1u, args.err);
-            if (ok) P::template tile<GUARD>(smem + st * P::kStageBytes, tpi, lane_j, iv, acc, eps2);
+            if (ok) P::template tile<GUARD>(smem + st * P::kStageBytes, tpi, lane_j, iv, acc, eps2, tbase + t);
             if (__syncthreads_or(!ok)) {
                 // A copy never completed: wait (bounded) for what is still in flight, then leave.
                 if (tid == 0) {
@@ -697,15 +732,16 @@ PlanParams plan_params(bool mixed, int64_t npad, int num_sms, int64_t pcap, int 
     q.b_force = b_force;
     q.c_tile = mixed ? 2 : 1;
     q.c_item = mixed ? 24 : 2;
-    // Mixed: the large-block kernel holds 3 i-particles per thread on half the
-    // threads per SM.  Its SMs evaluate ~9 % more pairs per second at m = N, so
-    // one of its thread iterations (3 pairs, 256 threads per SM) takes about
-    // (3 * 256) / (2 * 512) / 1.09 = 0.69 of a variant-0 iteration.
+    // Mixed: the large-block kernel holds 2 i-particles per thread on 2 CTAs per
+    // SM, the other 1 on 3.  Both are bound by the FP32 pipe, so a thread
+    // iteration (one j for each of its i) of the large-block kernel takes about
+    // (2 * 256) / (1 * 384) = 1.33 times as long when there are several waves of
+    // work items; with a single wave (latency-bound) ~1.7 times.
     q.variants = mixed ? 2 : 1;
     q.ipt1 = MixedWide::I;
     q.grid1 = mixed ? occupancy<MixedWide, false>() * num_sms : q.grid;
-    q.weight1 = 69;
-    q.weight1_one = 130;
+    q.weight1 = 133;
+    q.weight1_one = 170;
     for (int k = 0; k < kTuneBuckets; ++k) q.tuned[k] = -1;
     return q;
 }

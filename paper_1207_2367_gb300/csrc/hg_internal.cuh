@@ -37,24 +37,35 @@ struct State {
 };
 
 // ---------------------------------------------------------------------------
-// Predicted j-records ("j-data") in structure-of-arrays form, npad entries
-// (npad a multiple of the j-tile).  Entries n..npad-1 are zero-mass padding
-// far away from every particle, so tiles never need a bounds check.
-//   mixed: r0 = float4(x_hi, y_hi, z_hi, m)     r1 = float4(x_lo, y_lo, z_lo, a_x)
-//          r2 = float4(v_x, v_y, v_z, a_y)      r3 = float(a_z)          52 B/particle
+// Predicted j-records ("j-data"), npad entries (npad a multiple of the j-tile).
+// Entries n..npad-1 are zero-mass padding far away from every particle, so
+// tiles never need a bounds check.
+//   mixed: records are interleaved in pairs (2P, 2P+1), so that one 16-byte
+//          load gives the same two fields of both records as two register
+//          pairs for the packed FP32 (f32x2) arithmetic.  Seven arrays of
+//          npad / 2 entries, field f of record r at [r / 2].f[r % 2]:
+//          p0 = (x_hi, y_hi)  p1 = (z_hi, m)  p2 = (x_lo, y_lo)  p3 = (z_lo, a_x)
+//          p4 = (v_x, v_y)    p5 = (v_z, a_y)  (float4 each: f0 f0' f1 f1')
+//          p6 = (a_z)         (float2: f0 f0')                   52 B/particle
 //   fp64 : q0 = double2(x, y)  q1 = double2(z, m)  q2 = double2(v_x, v_y)
-//          q3 = double2(v_z, a_x)  q4 = double2(a_y, a_z)                   80 B/particle
+//          q3 = double2(v_z, a_x)  q4 = double2(a_y, a_z)          80 B/particle
 // ---------------------------------------------------------------------------
 struct Records {
-    void *p[5];
+    void *p[7];
+};
+constexpr int kMixedArrays = 7;
+
+// One mixed j-record (FP32 fields) and its place in the pair-interleaved arrays.
+struct MixedRecord {
+    float xh, yh, zh, m, xl, yl, zl, ax, vx, vy, vz, ay, az;
 };
 
 constexpr int kEvalThreads = 128;
 constexpr int kStages = 3;
 constexpr int kTJMixed = 256;   // j-records per shared-memory tile, mixed
 constexpr int kTJF64 = 128;     // j-records per shared-memory tile, fp64
-constexpr int kIMixed = 2;      // i-particles held per thread, mixed, small-block variant
-constexpr int kIMixedWide = 3;  // the same, large-block variant (fewer, register-heavier CTAs)
+constexpr int kIMixed = 1;      // i-particles held per thread, mixed, small-block variant
+constexpr int kIMixedWide = 2;  // the same, large-block variant (fewer, register-heavier CTAs)
 constexpr int kIF64 = 1;        // i-particles held per thread, fp64
 constexpr int kMaxTPI = 64;
 constexpr double kPadCoord = 1.0e18;
@@ -370,6 +381,76 @@ __device__ __forceinline__ float rsqrt_approx(float x)
     float y;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// Mixed j-record r in the pair-interleaved arrays.
+__device__ __forceinline__ void store_mixed_record(const Records &rec, int64_t r, const MixedRecord &v)
+{
+    const int64_t b = (r >> 1) * 4 + (r & 1);
+    float *const *a = reinterpret_cast<float *const *>(rec.p);
+    a[0][b] = v.xh; a[0][b + 2] = v.yh;
+    a[1][b] = v.zh; a[1][b + 2] = v.m;
+    a[2][b] = v.xl; a[2][b + 2] = v.yl;
+    a[3][b] = v.zl; a[3][b + 2] = v.ax;
+    a[4][b] = v.vx; a[4][b + 2] = v.vy;
+    a[5][b] = v.vz; a[5][b + 2] = v.ay;
+    a[6][(r >> 1) * 2 + (r & 1)] = v.az;
+}
+
+__device__ __forceinline__ MixedRecord load_mixed_record(const Records &rec, int64_t r)
+{
+    const int64_t b = (r >> 1) * 4 + (r & 1);
+    const float *const *a = reinterpret_cast<const float *const *>(rec.p);
+    MixedRecord v;
+    v.xh = __ldg(a[0] + b); v.yh = __ldg(a[0] + b + 2);
+    v.zh = __ldg(a[1] + b); v.m = __ldg(a[1] + b + 2);
+    v.xl = __ldg(a[2] + b); v.yl = __ldg(a[2] + b + 2);
+    v.zl = __ldg(a[3] + b); v.ax = __ldg(a[3] + b + 2);
+    v.vx = __ldg(a[4] + b); v.vy = __ldg(a[4] + b + 2);
+    v.vz = __ldg(a[5] + b); v.ay = __ldg(a[5] + b + 2);
+    v.az = __ldg(a[6] + (r >> 1) * 2 + (r & 1));
+    return v;
+}
+
+// Packed FP32 pairs (PTX f32x2, sm_100 and later): two floats in one 64-bit
+// register pair, each operation applied to both halves with FP32 rounding
+// (round to nearest even), exactly as two scalar operations.
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2_pack(float a, float b)
+{
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 f2_unpack(f2_t r)
+{
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b)
+{
+    f2_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b)
+{
+    f2_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b)
+{
+    f2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
+{
+    f2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
 }
 #endif
 

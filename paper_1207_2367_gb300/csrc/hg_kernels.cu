@@ -274,8 +274,7 @@ __device__ __forceinline__ void predict_record(const State &st, const Records &r
 {
     {
         if (MIXED) {
-            float4 r0, r1, r2;
-            float r3;
+            MixedRecord v;
             if (i < n) {
                 // Positions: FP64 Taylor series, then split into float hi + lo.
                 // Velocities and accelerations feed only the FP32 pair
@@ -296,21 +295,13 @@ __device__ __forceinline__ void predict_record(const State &st, const Records &r
                                  vf);
                     ap[k] = fmaf(hf, fmaf(hf, fmaf(hf, cf * (1.f / 6.f), sf * 0.5f), jf), af);
                 }
-                r0 = make_float4(hi[0], hi[1], hi[2], d2f(st.mass[i]));
-                r1 = make_float4(lo[0], lo[1], lo[2], ap[0]);
-                r2 = make_float4(vp[0], vp[1], vp[2], ap[1]);
-                r3 = ap[2];
+                v = MixedRecord{hi[0], hi[1], hi[2], d2f(st.mass[i]), lo[0], lo[1], lo[2], ap[0],
+                                vp[0], vp[1], vp[2], ap[1], ap[2]};
             } else {
                 const float far = (float)kPadCoord;
-                r0 = make_float4(far, far, far, 0.f);
-                r1 = make_float4(0.f, 0.f, 0.f, 0.f);
-                r2 = r1;
-                r3 = 0.f;
+                v = MixedRecord{far, far, far, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             }
-            static_cast<float4 *>(rec.p[0])[r] = r0;
-            static_cast<float4 *>(rec.p[1])[r] = r1;
-            static_cast<float4 *>(rec.p[2])[r] = r2;
-            static_cast<float *>(rec.p[3])[r] = r3;
+            store_mixed_record(rec, r, v);
         } else {
             double2 q0, q1, q2, q3, q4;
             if (i < n) {
@@ -1224,10 +1215,7 @@ __global__ void k_pad_records(Records rec, int64_t npad)
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npad; i += (int64_t)gridDim.x * blockDim.x) {
         if (MIXED) {
             const float far = (float)kPadCoord;
-            static_cast<float4 *>(rec.p[0])[i] = make_float4(far, far, far, 0.f);
-            static_cast<float4 *>(rec.p[1])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            static_cast<float4 *>(rec.p[2])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            static_cast<float *>(rec.p[3])[i] = 0.f;
+            store_mixed_record(rec, i, MixedRecord{far, far, far, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f});
         } else {
             static_cast<double2 *>(rec.p[0])[i] = make_double2(kPadCoord, kPadCoord);
             static_cast<double2 *>(rec.p[1])[i] = make_double2(kPadCoord, 0.0);

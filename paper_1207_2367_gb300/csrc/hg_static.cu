@@ -45,8 +45,7 @@ __global__ void k_pack(int64_t n, int64_t npad, const double *mass, const double
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npad; i += (int64_t)gridDim.x * blockDim.x) {
         if (MIXED) {
-            float4 r0, r1, r2;
-            float r3;
+            MixedRecord r;
             if (i < n) {
                 float hi[3], lo[3];
 #pragma unroll
@@ -54,22 +53,15 @@ __global__ void k_pack(int64_t n, int64_t npad, const double *mass, const double
                     hi[k] = __double2float_rn(x[3 * i + k]);
                     lo[k] = __double2float_rn(x[3 * i + k] - (double)hi[k]);
                 }
-                r0 = make_float4(hi[0], hi[1], hi[2], __double2float_rn(mass[i]));
-                r1 = make_float4(lo[0], lo[1], lo[2], __double2float_rn(a[3 * i]));
-                r2 = make_float4(__double2float_rn(v[3 * i]), __double2float_rn(v[3 * i + 1]),
-                                 __double2float_rn(v[3 * i + 2]), __double2float_rn(a[3 * i + 1]));
-                r3 = __double2float_rn(a[3 * i + 2]);
+                r = MixedRecord{hi[0], hi[1], hi[2], __double2float_rn(mass[i]), lo[0], lo[1], lo[2],
+                                __double2float_rn(a[3 * i]), __double2float_rn(v[3 * i]),
+                                __double2float_rn(v[3 * i + 1]), __double2float_rn(v[3 * i + 2]),
+                                __double2float_rn(a[3 * i + 1]), __double2float_rn(a[3 * i + 2])};
             } else {
                 const float far = (float)kPadCoord;
-                r0 = make_float4(far, far, far, 0.f);
-                r1 = make_float4(0.f, 0.f, 0.f, 0.f);
-                r2 = r1;
-                r3 = 0.f;
+                r = MixedRecord{far, far, far, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             }
-            static_cast<float4 *>(rec.p[0])[i] = r0;
-            static_cast<float4 *>(rec.p[1])[i] = r1;
-            static_cast<float4 *>(rec.p[2])[i] = r2;
-            static_cast<float *>(rec.p[3])[i] = r3;
+            store_mixed_record(rec, i, r);
         } else {
             double2 q0, q1, q2, q3, q4;
             if (i < n) {
@@ -189,11 +181,8 @@ extern "C" int hg_evaluate_static(int64_t n, const double *mass, const double *p
     const int64_t npad = (n + kTJMixed - 1) / kTJMixed * kTJMixed;
 
     Records rec{};
-    if (mixed) {
-        rec.p[0] = base;
-        rec.p[1] = base + npad * 16;
-        rec.p[2] = base + 2 * npad * 16;
-        rec.p[3] = base + 3 * npad * 16;
+    if (mixed) {   // six float4 arrays and one float2 array of npad / 2 record pairs
+        for (int q = 0; q < kMixedArrays; ++q) rec.p[q] = base + q * (npad / 2) * 16;
     } else {
         for (int q = 0; q < 5; ++q) rec.p[q] = base + q * npad * 16;
     }

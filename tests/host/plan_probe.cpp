@@ -16,16 +16,16 @@ int main(int argc, char **argv)
     q.i_per_thread = hg::kIMixed;
     q.ntiles = npad / q.tj;
     q.pcap = 4 * npad > (1 << 20) ? 4 * npad : (1 << 20);
-    q.grid = 4 * 152;
+    q.grid = 3 * 152;
     q.tpi_force = 0;
     q.b_force = 0;
     q.c_tile = 2;
     q.c_item = 24;
-    q.variants = 2;   // mixed: 2 and 3 i-particles per thread
+    q.variants = 2;   // mixed: 1 and 2 i-particles per thread
     q.ipt1 = hg::kIMixedWide;
     q.grid1 = 2 * 152;
-    q.weight1 = 69;
-    q.weight1_one = 130;
+    q.weight1 = 133;
+    q.weight1_one = 170;
     long long m;
     int v;
     while (scanf("%lld %d", &m, &v) == 2) {

@@ -163,7 +163,7 @@ def test_tune_rejects_bad_arguments(hg):
 
 @pytest.mark.parametrize("code", [0, 70, 165, 224, 224 + 33, 224 + 131, 224 + 194])
 def test_forced_table_matches_oracle_mixed(hg, code):
-    """Both mixed kernel variants (2 and 3 i-particles per thread) under forced
+    """Both mixed kernel variants (1 and 2 i-particles per thread) under forced
     plans: the mixed tolerances against the oracle."""
     n = 1000
     sysm = oracle_system(n, 75, EPS, steps=2)

@@ -58,7 +58,7 @@ def test_tuned_candidate_decodes_to_its_plan(probe, c):
     g = probe([(64, c)])[0]
     assert g["variant"] == variant
     assert g["tpi"] == 1 << (k // 32)
-    assert g["ti"] == 128 // g["tpi"] * (3 if variant else 2)
+    assert g["ti"] == 128 // g["tpi"] * (2 if variant else 1)
     assert g["tps"] == tps
     assert g["b"] == -(-ntiles // tps)
 
