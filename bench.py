@@ -40,11 +40,11 @@ FLOPS_F32 = 77     # FP32 adds + muls of the pair law per interaction (FMA = 2 f
 FLOPS_F64 = 77     # the same count for the FP64 path
 PAPER_FLOPS = 97   # the paper's count per interaction (82 SP + 15 DP)
 NUM_SMS = 152
-# DRAM bytes (read + write) of the evaluation per block step on the default
-# workload (both variant launches, the one the plan does not name returns at
-# once), from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, mean
-# over 100 block steps, cold L2).  Valid only while that kernel is unchanged.
-EVAL_TRAFFIC = {(65536, "equal", "mixed"): 3.55e6}
+# DRAM bytes (read + write) of the evaluation kernel per launch (one per block
+# step) on the default workload, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum, mean of 100 launches, cold L2).  Valid only while that
+# kernel is unchanged.
+EVAL_TRAFFIC = {(65536, "equal", "mixed"): 3.48e6}
 
 
 def parse_defaults():

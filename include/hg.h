@@ -242,14 +242,11 @@ int hg_evaluate_static(int64_t n, const double *mass, const double *pos, const d
  * Block sizes are grouped in HG_TUNE_BUCKETS buckets, bucket k holding
  * 2^k <= m < 2^(k+1).  For each bucket the table holds -1 (use the built-in
  * cost model) or a measured choice:
- *  - one system: a plan index c in [0, 224) (FP64) or [0, 448) (mixed); with
- *    v = c / 224 and k = c % 224, 2^(k / 32) threads share one i-particle and
- *    each j-chunk holds T[k % 32] j-tiles (256 records mixed, 128 FP64),
- *    T = {1, 2, ..., 16, 20, 24, 32, 40, 48, 64, 96, 128, 192, 256, 384, 512,
- *    1024, 2048, 4096, 8192}.  v selects the evaluation kernel: FP64 holds one
- *    i-particle per thread; mixed v = 0 two (4 CTAs per SM, for small blocks),
- *    v = 1 three (2 CTAs per SM, for large blocks).  The i-tile is 128 / 2^(k/32)
- *    times the particles per thread;
+ *  - one system: a plan index k in [0, 224): 2^(k / 32) threads share one
+ *    i-particle and each j-chunk holds T[k % 32] j-tiles (256 records mixed,
+ *    128 FP64), T = {1, 2, ..., 16, 20, 24, 32, 40, 48, 64, 96, 128, 192, 256,
+ *    384, 512, 1024, 2048, 4096, 8192}.  Both kernels hold one i-particle per
+ *    thread, so the i-tile is 128 / 2^(k/32) particles;
  *  - clusters (hg_init_batch): a code w + 8 (s + 1), w in [0, 6], s in
  *    {-1, 0, 1}: the j-split is the largest one leaving at least 2^w work items
  *    per resident CTA, and each cluster's threads per i-particle are 2^s times

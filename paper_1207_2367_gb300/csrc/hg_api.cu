@@ -215,7 +215,7 @@ int upload_scalar(hg_ctx *c, double *dev_field, double v)
 // evaluation (mixed: both kernel variants, one returns at once), reduction,
 // correction (with the next minimum); clusters, three next-block passes, batch
 // plan, prediction, evaluation, reduction, correction.
-int step_kernels(const hg_ctx *c) { return c->bv.nc > 0 ? 8 : (c->mixed ? 5 : 4); }
+int step_kernels(const hg_ctx *c) { return c->bv.nc > 0 ? 8 : 4; }
 
 // An event record that becomes a graph node when the stream is being captured
 // (a plain record inside a capture only orders work and cannot be timed).

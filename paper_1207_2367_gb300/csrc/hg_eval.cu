@@ -33,15 +33,16 @@ constexpr int kFold = 32;   // FP32 pair sums are folded into the compensated su
 // i-particle's values are duplicated into both halves once per work item.
 // One packed instruction does the FP32 work of two, so the issue slots per
 // pair interaction halve and the FP32 pipe (not instruction issue) becomes
-// the limit.  IPT i-particles per thread: 1 for small and medium blocks
-// (short latency, more CTAs per SM), 2 for large ones.
+// the limit.  One i-particle per thread, 3 CTAs per SM: measured against two
+// per thread (2 CTAs per SM), two j-pairs per iteration, and 4 CTAs per SM,
+// it was as fast or faster for every block size.
 template <int IPT>
 struct Mixed {
     static constexpr int TJ = kTJMixed;
     static constexpr int TP = TJ / 2;   // record pairs per tile
     static constexpr int I = IPT;
-    static constexpr int kMinBlocks = IPT == kIMixed ? 3 : 2;
-    static constexpr int kVariant = IPT == kIMixed ? 0 : 1;
+    static constexpr int kMinBlocks = 3;
+    static constexpr int kVariant = 0;
     static constexpr uint32_t kStageBytes = TJ * 52;
     struct IData {
         f2_t xh, yh, zh, xl, yl, zl, vx, vy, vz, ax, ay, az;   // (v, v) duplicated
@@ -425,7 +426,6 @@ struct F64 {
 };
 
 typedef Mixed<kIMixed> MixedEval;
-typedef Mixed<kIMixedWide> MixedWide;
 
 template <class P>
 constexpr size_t smem_bytes()
@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
     const BatchView &bv = args.bv;
     const bool batch = bv.nc > 0;
     const Plan pl = args.plan_dev ? *args.plan_dev : args.plan_host;
-    if (!batch && pl.variant != P::kVariant) return;   // the plan runs on the other kernel
+    if (!batch && pl.variant != P::kVariant) return;   // a plan for another kernel (none at present)
     const int64_t n_items = batch ? bv.item_off[bv.nc] : pl.n_items;
     const int64_t tps = batch ? *bv.tps : pl.tiles_per_split;
     if ((int64_t)blockIdx.x >= n_items) return;
@@ -663,8 +663,6 @@ cudaError_t eval_setup(int)
     cudaError_t e;
     if ((e = set_attr<MixedEval, false>()) != cudaSuccess) return e;
     if ((e = set_attr<MixedEval, true>()) != cudaSuccess) return e;
-    if ((e = set_attr<MixedWide, false>()) != cudaSuccess) return e;
-    if ((e = set_attr<MixedWide, true>()) != cudaSuccess) return e;
     if ((e = set_attr<F64, false>()) != cudaSuccess) return e;
     return set_attr<F64, true>();
 }
@@ -695,19 +693,12 @@ int clip_grid(const EvalArgs &args, int num_sms)
 }
 }  // namespace
 
-int eval_launches(bool mixed, const EvalArgs &args) { return (mixed && args.bv.nc == 0) ? 2 : 1; }
+int eval_launches(bool, const EvalArgs &) { return 1; }
 
 cudaError_t launch_eval(bool mixed, const EvalArgs &args, int num_sms, cudaStream_t st)
 {
     if (!mixed) return launch_one<F64>(args, clip_grid<F64>(args, num_sms), st);
-    const bool batch = args.bv.nc > 0;
-    if (batch) return launch_one<MixedEval>(args, clip_grid<MixedEval>(args, num_sms), st);
-    if (!args.plan_dev)
-        return args.plan_host.variant == 1 ? launch_one<MixedWide>(args, clip_grid<MixedWide>(args, num_sms), st)
-                                           : launch_one<MixedEval>(args, clip_grid<MixedEval>(args, num_sms), st);
-    cudaError_t e = launch_one<MixedEval>(args, clip_grid<MixedEval>(args, num_sms), st);
-    if (e != cudaSuccess) return e;
-    return launch_one<MixedWide>(args, clip_grid<MixedWide>(args, num_sms), st);
+    return launch_one<MixedEval>(args, clip_grid<MixedEval>(args, num_sms), st);
 }
 
 cudaError_t launch_reduce(const EvalArgs &args, double *ra, double *rj, double *rs, int grid, cudaStream_t st)
@@ -732,16 +723,11 @@ PlanParams plan_params(bool mixed, int64_t npad, int num_sms, int64_t pcap, int 
     q.b_force = b_force;
     q.c_tile = mixed ? 2 : 1;
     q.c_item = mixed ? 24 : 2;
-    // Mixed: the large-block kernel holds 2 i-particles per thread on 2 CTAs per
-    // SM, the other 1 on 3.  Both are bound by the FP32 pipe, so a thread
-    // iteration (one j for each of its i) of the large-block kernel takes about
-    // (2 * 256) / (1 * 384) = 1.33 times as long when there are several waves of
-    // work items; with a single wave (latency-bound) ~1.7 times.
-    q.variants = mixed ? 2 : 1;
-    q.ipt1 = MixedWide::I;
-    q.grid1 = mixed ? occupancy<MixedWide, false>() * num_sms : q.grid;
-    q.weight1 = 133;
-    q.weight1_one = 170;
+    // One kernel per precision (the planner's second-variant fields unused).
+    q.variants = 1;
+    q.ipt1 = q.i_per_thread;
+    q.grid1 = q.grid;
+    q.weight1 = q.weight1_one = 100;
     for (int k = 0; k < kTuneBuckets; ++k) q.tuned[k] = -1;
     return q;
 }

@@ -64,8 +64,7 @@ constexpr int kEvalThreads = 128;
 constexpr int kStages = 3;
 constexpr int kTJMixed = 256;   // j-records per shared-memory tile, mixed
 constexpr int kTJF64 = 128;     // j-records per shared-memory tile, fp64
-constexpr int kIMixed = 1;      // i-particles held per thread, mixed, small-block variant
-constexpr int kIMixedWide = 2;  // the same, large-block variant (fewer, register-heavier CTAs)
+constexpr int kIMixed = 1;      // i-particles held per thread, mixed
 constexpr int kIF64 = 1;        // i-particles held per thread, fp64
 constexpr int kMaxTPI = 64;
 constexpr double kPadCoord = 1.0e18;
@@ -266,10 +265,9 @@ void set_call_error(const char *msg);
 // Host-side launchers (hg_eval.cu).
 cudaError_t eval_setup(int device);
 int eval_grid(bool mixed, int num_sms);
-// Evaluation of args.  Host plan: the plan's kernel variant on min(items, its
-// grid) CTAs (clusters: variant 0 on its full grid).  Device plan (graph steps):
-// every variant of the precision on its full grid; the ones the plan does not
-// name return at once.
+// Evaluation of args: the precision's kernel on min(items, its grid) CTAs with
+// a host plan, on its full persistent grid with a device plan (graph steps) or
+// clusters.
 cudaError_t launch_eval(bool mixed, const EvalArgs &args, int num_sms, cudaStream_t st);
 // Kernels launch_eval issues for a device plan.
 int eval_launches(bool mixed, const EvalArgs &args);

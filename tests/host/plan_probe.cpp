@@ -21,11 +21,10 @@ int main(int argc, char **argv)
     q.b_force = 0;
     q.c_tile = 2;
     q.c_item = 24;
-    q.variants = 2;   // mixed: 1 and 2 i-particles per thread
-    q.ipt1 = hg::kIMixedWide;
-    q.grid1 = 2 * 152;
-    q.weight1 = 133;
-    q.weight1_one = 170;
+    q.variants = 1;   // one mixed kernel, one i-particle per thread
+    q.ipt1 = hg::kIMixed;
+    q.grid1 = q.grid;
+    q.weight1 = q.weight1_one = 100;
     long long m;
     int v;
     while (scanf("%lld %d", &m, &v) == 2) {

@@ -48,32 +48,23 @@ def test_untuned_value_keeps_the_cost_model(probe):
         assert (g["w_log"], g["tpi_shift"]) == (1, 0)
 
 
-@pytest.mark.parametrize("c", [0, 5, 33, 70, 100, 150, 200, 224, 224 + 33, 224 + 165])
+@pytest.mark.parametrize("c", [0, 5, 33, 70, 100, 150, 200, 223])
 def test_tuned_candidate_decodes_to_its_plan(probe, c):
     ntiles = 65536 // 256
-    variant, k = divmod(c, 224)
-    tps = TPS[k % 32]
+    tps = TPS[c % 32]
     if tps > ntiles:
         pytest.skip("candidate not admissible at this size")
     g = probe([(64, c)])[0]
-    assert g["variant"] == variant
-    assert g["tpi"] == 1 << (k // 32)
-    assert g["ti"] == 128 // g["tpi"] * (2 if variant else 1)
+    assert g["variant"] == 0
+    assert g["tpi"] == 1 << (c // 32)
+    assert g["ti"] == 128 // g["tpi"]
     assert g["tps"] == tps
     assert g["b"] == -(-ntiles // tps)
 
 
-def test_large_blocks_choose_the_wide_kernel(probe):
-    # the cost model gives small blocks to the 2-per-thread kernel and whole
-    # systems to the 3-per-thread one
-    small, large = probe([(1, -1), (1 << 23, -1)], npad=1 << 23)
-    assert small["model_variant"] == 0
-    assert large["model_variant"] == 1
-
-
 def test_inadmissible_tuned_value_falls_back_to_the_model(probe):
-    # tps 8192 > 256 tiles, and values outside [0, 448): both fall back.
-    for v in (31, 224 + 31, 448, 5000):
+    # tps 8192 > 256 tiles, and values outside [0, 224): both fall back.
+    for v in (31, 224, 224 + 33, 5000):
         g = probe([(100, v)])[0]
         assert (g["tpi"], g["tps"]) == (g["model_tpi"], g["model_tps"])
 
