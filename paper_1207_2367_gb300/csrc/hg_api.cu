@@ -3,6 +3,7 @@
 // stepping loop.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stddef.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -33,6 +34,8 @@ struct hg_ctx {
     double *nb_part = nullptr;
     DevScalars *d_sc = nullptr, *h_sc = nullptr;   // h_sc: pinned host mirror
     double *h_stage = nullptr;                     // pinned staging for small uploads
+    int32_t *h_flags = nullptr;                    // pinned: (done, err) after two recent replays
+    cudaEvent_t ev_flags[2] = {nullptr, nullptr};  // completion of those copies
     double *partial = nullptr;
     int64_t pcap = 0;
     PlanParams pp{};      // evaluation planner inputs
@@ -241,7 +244,8 @@ int enqueue_block_step(hg_ctx *c, cudaStream_t s, const cudaEvent_t *ev)
     if (batch)
         HG_CUDA(c, launch_predict_clusters(c->mixed, c->st, c->rec, c->n, c->bv, &c->d_sc->t_cur, &c->d_sc->m, s));
     else
-        HG_CUDA(c, launch_predict_select(c->mixed, c->st, c->rec, c->n, c->npad, c->d_idx, c->d_sc, 1, c->pp, s));
+        HG_CUDA(c, launch_predict_select(c->mixed, c->st, c->rec, c->n, c->npad, c->d_idx, c->d_sc, 1, c->pp,
+                                         4 * c->num_sms, s));
     if (ev) HG_CUDA(c, record_external(ev[2], s));
     EvalArgs a = eval_args(c, &c->d_sc->m, 0);
     HG_CUDA(c, launch_eval(c->mixed, a, c->num_sms, s));
@@ -348,6 +352,9 @@ void release(hg_ctx *c)
     for (void *p : c->dev_allocs) cudaFree(p);
     if (c->h_sc) cudaFreeHost(c->h_sc);
     if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->h_flags) cudaFreeHost(c->h_flags);
+    for (cudaEvent_t e : c->ev_flags)
+        if (e) cudaEventDestroy(e);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     cudaGetLastError();
@@ -370,6 +377,8 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
     HG_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
     HG_CUDA(c, cudaMallocHost(reinterpret_cast<void **>(&c->h_sc), sizeof(DevScalars)));
     HG_CUDA(c, cudaMallocHost(reinterpret_cast<void **>(&c->h_stage), 4 * sizeof(double)));
+    HG_CUDA(c, cudaMallocHost(reinterpret_cast<void **>(&c->h_flags), 4 * sizeof(int32_t)));
+    for (cudaEvent_t &e : c->ev_flags) HG_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 
     const int64_t tj = kTJMixed > kTJF64 ? kTJMixed : kTJF64;
     c->npad = (n + tj - 1) / tj * tj;
@@ -908,12 +917,36 @@ int hg_advance(hg_ctx *c, double t_end, int64_t *steps_out)
     rc = upload_scalar(c, &c->d_sc->t_stop, t_end);
     if (rc) return rc;
     HG_CUDA(c, cudaMemsetAsync(&c->d_sc->done, 0, sizeof(int32_t), c->stream));
-    for (;;) {
-        rc = replay(c, true);
-        if (rc) break;
-        rc = sync_scalars(c);
-        if (rc) break;
-        if (c->h_sc->done) break;
+    if (c->opts.profile) {   // profiled replays synchronise anyway: check after each
+        for (;;) {
+            rc = replay(c, true);
+            if (rc) break;
+            rc = sync_scalars(c);
+            if (rc) break;
+            if (c->h_sc->done) break;
+        }
+    } else {
+        // Keep the next replay queued while the flags of the previous one are
+        // read, so that the GPU never waits for the host.  Replays past the
+        // stop time are empty block steps (m = 0, every kernel returns at
+        // once): at most one such graph runs per call.
+        static_assert(offsetof(DevScalars, err) == offsetof(DevScalars, done) + sizeof(int32_t),
+                      "done and err are adjacent");
+        for (int64_t k = 0;; ++k) {
+            const int slot = (int)(k & 1);
+            if ((rc = replay(c, true)) != HG_OK) break;
+            int32_t *flags = c->h_flags + 2 * slot;
+            HG_CUDA(c, cudaMemcpyAsync(flags, &c->d_sc->done, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                       c->stream));
+            HG_CUDA(c, cudaEventRecord(c->ev_flags[slot], c->stream));
+            if (k == 0) continue;
+            const int prev = slot ^ 1;
+            HG_CUDA(c, cudaEventSynchronize(c->ev_flags[prev]));
+            const int32_t *pf = c->h_flags + 2 * prev;
+            if (pf[1] & ERR_TIMEOUT) break;   // reported by the final read below
+            if (pf[0]) break;
+        }
+        if (rc == HG_OK) rc = sync_scalars(c);
     }
     int rc2 = upload_scalar(c, &c->d_sc->t_stop, INFINITY);
     if (rc) return rc;

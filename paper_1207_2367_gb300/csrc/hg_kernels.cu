@@ -276,21 +276,28 @@ __device__ __forceinline__ void predict_record(const State &st, const Records &r
         if (MIXED) {
             MixedRecord v;
             if (i < n) {
-                // Positions: FP64 Taylor series, then split into float hi + lo.
+                // Positions: x + h v in FP64 plus the rest of the Taylor series,
+                // h^2 (a/2 + h (j/6 + h (s/24 + h c/120))), as an FP32 Horner
+                // series (its rounding, ~5e-7 of a term that is itself a small
+                // part of the step's displacement, stays far below the FP32 pair
+                // error), then split into float hi + lo: 3 FP64 instructions per
+                // component, the FP64 pipe being this kernel's limit on GB300.
                 // Velocities and accelerations feed only the FP32 pair
                 // arithmetic: FP32 Horner series from the rounded derivatives.
                 const double h = tt - st.t[i];
-                const double h2 = h * h * 0.5, h3 = h2 * h * (1.0 / 3.0), h4 = h3 * h * 0.25, h5 = h4 * h * 0.2;
                 const float hf = d2f(h);
                 float hi[3], lo[3], vp[3], ap[3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const int64_t q = 3 * i + k;
                     const double x = st.x[q], v = st.v[q], a = st.a[q], j = st.j[q], s = st.s[q], c = st.c[q];
-                    const double xp = x + fma(h, v, fma(h2, a, fma(h3, j, fma(h4, s, h5 * c))));
+                    const float vf = d2f(v), af = d2f(a), jf = d2f(j), sf = d2f(s), cf = d2f(c);
+                    const float rest =
+                        hf * hf *
+                        fmaf(hf, fmaf(hf, fmaf(hf, cf * (1.f / 120.f), sf * (1.f / 24.f)), jf * (1.f / 6.f)), af * 0.5f);
+                    const double xp = fma(h, v, x) + f2d(rest);
                     hi[k] = d2f(xp);
                     lo[k] = d2f(xp - f2d(hi[k]));
-                    const float vf = d2f(v), af = d2f(a), jf = d2f(j), sf = d2f(s), cf = d2f(c);
                     vp[k] = fmaf(hf, fmaf(hf, fmaf(hf, fmaf(hf, cf * (1.f / 24.f), sf * (1.f / 6.f)), jf * 0.5f), af),
                                  vf);
                     ap[k] = fmaf(hf, fmaf(hf, fmaf(hf, cf * (1.f / 6.f), sf * 0.5f), jf), af);
@@ -369,7 +376,7 @@ __global__ void k_predict_clusters(const State st, const Records rec, int64_t n,
 // the counters and the evaluation plan, and clears the minimum for the next
 // correction.  t_next > t_stop: no step (m = 0, done).
 template <bool MIXED>
-__global__ void __launch_bounds__(64) k_predict_select(const State st, const Records rec, int64_t n, int64_t npad,
+__global__ void __launch_bounds__(256) k_predict_select(const State st, const Records rec, int64_t n, int64_t npad,
                                                        int32_t *idx, DevScalars *sc, int count_step,
                                                        const PlanParams pq)
 {
@@ -1284,13 +1291,17 @@ cudaError_t launch_predict(bool mixed, const State &st, const Records &rec, int6
 }
 
 cudaError_t launch_predict_select(bool mixed, const State &st, const Records &rec, int64_t n, int64_t npad,
-                                  int32_t *idx, DevScalars *sc, int count_step, const PlanParams &pq, cudaStream_t s)
+                                  int32_t *idx, DevScalars *sc, int count_step, const PlanParams &pq, int max_grid,
+                                  cudaStream_t s)
 {
-    const int g = grid_for(npad, 64, 1 << 20);
+    // Persistent grid: every CTA takes one atomic on the arrival counter, and
+    // at N = 2^20 sixteen thousand of them on one address cost more than the
+    // prediction itself.
+    const int g = grid_for(npad, 256, max_grid);
     if (mixed)
-        k_predict_select<true><<<g, 64, 0, s>>>(st, rec, n, npad, idx, sc, count_step, pq);
+        k_predict_select<true><<<g, 256, 0, s>>>(st, rec, n, npad, idx, sc, count_step, pq);
     else
-        k_predict_select<false><<<g, 64, 0, s>>>(st, rec, n, npad, idx, sc, count_step, pq);
+        k_predict_select<false><<<g, 256, 0, s>>>(st, rec, n, npad, idx, sc, count_step, pq);
     return cudaGetLastError();
 }
 

@@ -29,7 +29,8 @@ cudaError_t launch_next_min(const State &st, int64_t n, double *part, DevScalars
 // min_pass); predicts every record to t_next, lists the due particles in idx
 // (arbitrary order), sets m, t_cur, done, the counters and the plan.
 cudaError_t launch_predict_select(bool mixed, const State &st, const Records &rec, int64_t n, int64_t npad,
-                                  int32_t *idx, DevScalars *sc, int count_step, const PlanParams &pq, cudaStream_t s);
+                                  int32_t *idx, DevScalars *sc, int count_step, const PlanParams &pq, int max_grid,
+                                  cudaStream_t s);
 // tend = t + dt after the state was replaced.
 cudaError_t launch_tend(const State &st, int64_t n, cudaStream_t s);
 // rmap: record of each particle (clusters), or nullptr (record i = particle i).
