@@ -369,8 +369,9 @@ def run_ours(a, rank, world, dist):
         "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if mixed else "f64", "data": "synthetic",
         "config": {"workload": workload_name(a), "n": a.n,
-                   "precision": ("mixed: f32 pair arithmetic, double-single dr, Kahan f32 sums folded into f64, "
-                                 "f64 state/predictor/corrector" if mixed else "f64 throughout"),
+                   "precision": ("mixed: f32 pair arithmetic (packed f32x2, two pairs per instruction), "
+                                 "double-single dr, Kahan f32 sums widened to f64, f64 state/corrector, "
+                                 "f64 x + h v in the predictor" if mixed else "f64 throughout"),
                    "l2": "flushed between timed steps (256 MB write outside the timed events); "
                          "inputs resident in HBM",
                    "parallelism": f"replicas x{world}"},
