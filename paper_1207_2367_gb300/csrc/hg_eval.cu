@@ -35,7 +35,7 @@ constexpr int kFold = 32;   // FP32 pair sums are folded into the compensated su
 // pair interaction halve and the FP32 pipe (not instruction issue) becomes
 // the limit.  One i-particle per thread, 3 CTAs per SM: measured against two
 // per thread (2 CTAs per SM), two j-pairs per iteration, and 4 CTAs per SM,
-// it was as fast or faster for every block size.
+// it was faster overall and within 1 % where another form won.
 template <int IPT>
 struct Mixed {
     static constexpr int TJ = kTJMixed;
