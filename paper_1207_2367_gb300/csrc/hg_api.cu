@@ -621,16 +621,11 @@ int tune_impl(hg_ctx *c, int64_t m_max, int32_t reps_in, hg_tune_entry *report, 
     int32_t count = 0;
     std::vector<int32_t> list;
     for (int k = 0; k <= tune_bucket(mtop) && rc == HG_OK; ++k) {
-        // A fixed plan serves the whole bucket, and its wave count jumps with
-        // m, so it is timed at block sizes spread over the bucket: 2^k (5/4,
-        // 3/2, 7/4), clamped to mtop; the reported m is the middle one.
+        // Timed at block sizes spread over the bucket (tune_points); the
+        // reported m is the bucket's middle one.
         const int64_t m = k == 0 ? 1 : std::min<int64_t>(mtop, (int64_t)3 << (k - 1));
-        std::vector<int64_t> pts;
-        if (k == 0) pts = {1};
-        else if (k == 1) pts = {2, std::min<int64_t>(mtop, 3)};
-        else
-            for (int64_t f = 5; f <= 7; ++f) pts.push_back(std::min<int64_t>(mtop, (f << k) / 4));
-        pts.erase(std::unique(pts.begin(), pts.end()), pts.end());
+        int64_t pts_a[3];
+        const std::vector<int64_t> pts(pts_a, pts_a + tune_points(k, mtop, pts_a));
         const std::vector<int> cand = tune_candidates(c, m);
         std::vector<double> sum(cand.size(), 0.0);
         for (size_t pi = 0; pi < pts.size() && rc == HG_OK; ++pi) {

@@ -111,6 +111,31 @@ __host__ __device__ inline int tune_bucket(int64_t m)
     return k;
 }
 
+// Block sizes at which the autotuner times every candidate plan of bucket k
+// (2^k <= m < 2^(k+1)), the largest size tuned being mtop.  A stored plan serves
+// the whole bucket and its wave count jumps with m, so one size is not enough:
+// k = 0: 1; k = 1: 2, 3; k >= 2: 2^k * 5/4, 3/2, 7/4; each clamped to mtop,
+// repeats dropped.  Returns how many (1 to 3).
+__host__ __device__ inline int tune_point_add(int64_t v, int64_t mtop, int64_t (&pts)[3], int np)
+{
+    v = v < mtop ? v : mtop;
+    if (np == 0 || pts[np - 1] != v) pts[np++] = v;
+    return np;
+}
+__host__ __device__ inline int tune_points(int k, int64_t mtop, int64_t (&pts)[3])
+{
+    int np = 0;
+    if (k == 0) {
+        np = tune_point_add(1, mtop, pts, np);
+    } else if (k == 1) {
+        np = tune_point_add(2, mtop, pts, np);
+        np = tune_point_add(3, mtop, pts, np);
+    } else {
+        for (int64_t f = 5; f <= 7; ++f) np = tune_point_add((f << k) / 4, mtop, pts, np);
+    }
+    return np;
+}
+
 // Candidate c in [0, variants * kPlanCandidates): variant c / kPlanCandidates,
 // threads per i = 2^((c % kPlanCandidates) / 32), tiles per split plan_tps(c % 32).
 constexpr int kPlanCandidates = 7 * 32;

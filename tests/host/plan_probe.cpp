@@ -1,6 +1,8 @@
 // Host-side check of the evaluation planner (hg_internal.cuh): prints, for
 // each query line "m tuned_value" read from stdin, the bucket and the plan
-// chosen with that value stored in m's bucket ("-" for the cost model alone).
+// chosen with that value stored in m's bucket ("-" for the cost model alone),
+// and the block sizes the autotuner would time for that bucket with m as the
+// largest size tuned.
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -34,8 +36,13 @@ int main(int argc, char **argv)
         q.tuned[b] = (int16_t)v;
         const hg::Plan p = hg::make_plan(m, q);
         const hg::BatchKnobs kn = hg::batch_knobs(m, q);
-        printf("%d %d %lld %d %lld %d %d %d %d %d %d\n", b, model.tpi, (long long)model.tiles_per_split, p.tpi,
-               (long long)p.tiles_per_split, p.b, kn.w_log, kn.tpi_shift, p.variant, p.ti, model.variant);
+        long long pts[3] = {0, 0, 0};
+        int64_t pt[3];
+        const int np = hg::tune_points(b, m, pt);   // this bucket's tuning sizes, m as the largest
+        for (int k = 0; k < np; ++k) pts[k] = (long long)pt[k];
+        printf("%d %d %lld %d %lld %d %d %d %d %d %d %d %lld %lld %lld\n", b, model.tpi,
+               (long long)model.tiles_per_split, p.tpi, (long long)p.tiles_per_split, p.b, kn.w_log, kn.tpi_shift,
+               p.variant, p.ti, model.variant, np, pts[0], pts[1], pts[2]);
     }
     return 0;
 }

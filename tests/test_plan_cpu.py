@@ -31,7 +31,7 @@ def probe(tmp_path_factory):
         text = "".join(f"{m} {v}\n" for m, v in queries)
         out = subprocess.run([exe, str(npad)], input=text, capture_output=True, text=True, check=True).stdout
         keys = ("bucket", "model_tpi", "model_tps", "tpi", "tps", "b", "w_log", "tpi_shift", "variant", "ti",
-                "model_variant")
+                "model_variant", "n_points", "p0", "p1", "p2")
         return [dict(zip(keys, map(int, line.split()))) for line in out.splitlines()]
     return run
 
@@ -77,3 +77,25 @@ def test_batch_codes_decode(probe):
     for bad in (7, 15, 24, 40):   # w > 6 or s > 1: the untuned knobs
         g = probe([(300, bad)])[0]
         assert (g["w_log"], g["tpi_shift"]) == (1, 0)
+
+
+def test_tuning_points_span_each_bucket(probe):
+    """The autotuner times a bucket's plans at 5/4, 3/2 and 7/4 of 2^k (a plan
+    stored for the bucket must hold for every m in it, and its wave count jumps
+    with m); the first two buckets at their own sizes; all clamped to the
+    largest tuned size."""
+    big = 1 << 20
+    for k in range(2, 20):
+        g = probe([((1 << (k + 1)) - 1, -1)], npad=big)[0]   # m = top of bucket k: no clamping
+        assert g["bucket"] == k
+        assert (g["n_points"], g["p0"], g["p1"], g["p2"]) == (3, 5 << k >> 2, 3 << k >> 1, 7 << k >> 2)
+        assert all((1 << k) <= p < (1 << (k + 1)) for p in (g["p0"], g["p1"], g["p2"]))
+    g0, g1 = probe([(1, -1), (3, -1)])
+    assert (g0["n_points"], g0["p0"]) == (1, 1)
+    assert (g1["n_points"], g1["p0"], g1["p1"]) == (2, 2, 3)
+    # m = 2: bucket 1 clamped to 2, a single size; m = 5 (bucket 2 = [4, 7]): 5, then 6 and 7 clamp to 5
+    g2, g5 = probe([(2, -1), (5, -1)])
+    assert (g2["n_points"], g2["p0"]) == (1, 2)
+    assert (g5["n_points"], g5["p0"]) == (1, 5)
+    g6 = probe([(6, -1)])[0]
+    assert (g6["n_points"], g6["p0"], g6["p1"]) == (2, 5, 6)
