@@ -215,9 +215,8 @@ int upload_scalar(hg_ctx *c, double *dev_field, double v)
 }
 
 // Kernels per graph-replayed block step: one system, selection + prediction,
-// evaluation (mixed: both kernel variants, one returns at once), reduction,
-// correction (with the next minimum); clusters, three next-block passes, batch
-// plan, prediction, evaluation, reduction, correction.
+// evaluation, reduction, correction (with the next minimum); clusters, three
+// next-block passes, batch plan, prediction, evaluation, reduction, correction.
 int step_kernels(const hg_ctx *c) { return c->bv.nc > 0 ? 8 : 4; }
 
 // An event record that becomes a graph node when the stream is being captured
@@ -468,9 +467,8 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
     c->e_out = dalloc<double>(c, 2);
     c->l_part = dalloc<double>(c, 3 * c->e_g2);
     c->l_out = dalloc<double>(c, 3);
-    ok = ok && c->d_idx && c->d_idx2 && c->nb_part && c->nb_cnt && c->nb_off && c->d_sc && c->partial && c->ra && c->rn &&
-         c->rj &&
-         c->rs && c->xe && c->ve && c->phi_part && c->e_part && c->e_out && c->l_part && c->l_out;
+    ok = ok && c->d_idx && c->d_idx2 && c->nb_part && c->nb_cnt && c->nb_off && c->d_sc && c->partial && c->ra &&
+         c->rj && c->rs && c->rn && c->xe && c->ve && c->phi_part && c->e_part && c->e_out && c->l_part && c->l_out;
     if (!ok) return fail(c, HG_ENOMEM, "device allocation failed");
 
     HG_CUDA(c, eval_setup(c->device));
