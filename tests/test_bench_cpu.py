@@ -1,0 +1,31 @@
+"""Host logic of bench.py that needs no GPU: the paper's block-size groups of the
+cost attribution (Sect. 5.5).  The text's group bounds overlap at 1k, 10k and
+100k; the reading used is A [1, 20], B [21, 100], C [101, 1000], D [1001, 10^4],
+E [10^4 + 1, 10^5], F above."""
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def test_groups_partition_the_block_sizes():
+    edges = {1: "A", 20: "A", 21: "B", 100: "B", 101: "C", 1000: "C", 1001: "D", 10000: "D",
+             10001: "E", 100000: "E", 100001: "F", 1 << 23: "F"}
+    for m, g in edges.items():
+        assert bench.paper_group(m) == g, m
+    ranges = sorted(bench.PAPER_GROUPS.values())
+    assert ranges[0][0] == 1
+    for (lo0, hi0), (lo1, hi1) in zip(ranges, ranges[1:]):
+        assert lo1 == hi0 + 1          # contiguous, no overlap
+        assert lo1 <= hi1
+
+
+def test_relative_error_statistics():
+    import numpy as np
+    ref = np.array([[3.0, 4.0, 0.0], [0.0, 0.0, 2.0]])
+    got = ref + np.array([[0.0, 0.0, 5e-7], [0.0, 0.0, 2e-6]])
+    st = bench._rel_stats(got, ref)
+    assert abs(st["max"] - 1e-6) < 1e-15            # particle 2: 2e-6 / 2
+    assert abs(st["median"] - 0.5 * (1e-7 + 1e-6)) < 1e-15
+    assert abs(st["normwise"] - np.sqrt(5e-7 ** 2 + 2e-6 ** 2) / np.sqrt(25.0 + 4.0)) < 1e-15
