@@ -29,3 +29,19 @@ def test_relative_error_statistics():
     assert abs(st["max"] - 1e-6) < 1e-15            # particle 2: 2e-6 / 2
     assert abs(st["median"] - 0.5 * (1e-7 + 1e-6)) < 1e-15
     assert abs(st["normwise"] - np.sqrt(5e-7 ** 2 + 2e-6 ** 2) / np.sqrt(25.0 + 4.0)) < 1e-15
+
+
+def test_clock_samples_and_throttle_reasons():
+    lines = [
+        "0, 2070, 2070, 950.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "0, 2055, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n",
+        "0, 2070, 2070, 1010.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n",
+        "0, [N/A], 2070, [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]\n",   # unreadable sample: skipped
+        "garbage\n",
+    ]
+    out = bench.parse_clock_samples(lines)
+    assert out["samples"] == 3 and out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+    hot = bench.parse_clock_samples(["0, 1500, 2070, 1400, 0x48, Active, Active, Not Active, Not Active\n"])
+    assert hot["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
+    assert bench.parse_clock_samples([])["reasons"] == ["no samples"]
