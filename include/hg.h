@@ -37,8 +37,11 @@ extern "C" {
 #define HG_ETIMEOUT 5   /* a bounded device-side wait expired; results are invalid */
 
 #define HG_FP64 0       /* FP64 pair arithmetic and FP64 sums */
-#define HG_MIXED 1      /* FP32 pair arithmetic, double-single position differences,
-                           compensated FP32 sums folded into FP64; FP64 state */
+#define HG_MIXED 1      /* FP32 pair arithmetic (two pairs per packed f32x2 instruction),
+                           double-single position differences, compensated FP32 sums
+                           widened to FP64; FP64 state and corrector.  The step criterion
+                           may not shrink a step whose 4th-order residual lies below
+                           3e-6 sum_j m_j / (r_ij^2 + eps^2), the evaluation's noise scale */
 
 typedef struct hg_ctx hg_ctx;
 
@@ -159,7 +162,11 @@ int hg_step(hg_ctx *ctx, int64_t n_steps);
 
 /* Block steps until the next block time would exceed t_end (choose t_end a
  * multiple of dt_max to end with every particle at t_end).  *steps_out, if
- * non-NULL, receives the number of block steps taken.  Synchronizes. */
+ * non-NULL, receives the number of block steps taken.  Graphs of graph_steps
+ * block steps are replayed with the next one queued while the host reads the
+ * previous one's stop flag, so up to one graph of empty steps (m = 0, every
+ * kernel returns at once) runs past t_end; they change nothing and are not
+ * counted as block steps.  Synchronizes. */
 int hg_advance(hg_ctx *ctx, double t_end, int64_t *steps_out);
 
 /* Kinetic and potential energy (Sect. 2 softened potential, W = -sum_{i<j}
