@@ -129,6 +129,48 @@ def test_condition_scale_equals_norm_when_terms_are_aligned():
     assert np.all(sc[:, 2] >= np.linalg.norm(S, axis=1) * (1 - 1e-15))
 
 
+@pytest.mark.parametrize("eps", [0.0, 0.3])
+def test_condition_scale_columns_equal_mpmath_pair_derivatives(eps):
+    """The condition scale (acc, jerk and snap columns) sums over j of the norms of
+    each pair's acceleration m_j r_ij / (r_ij^2 + eps^2)^(3/2) and of its 1st and
+    2nd time derivatives along prescribed cubic trajectories (mpmath, 40 digits):
+    the pair terms whose sums are acc, jerk and snap."""
+    mp.mp.dps = 40
+    n = 4
+    c0 = rng.normal(size=(n, 3)) * 1.5
+    c1 = rng.normal(size=(n, 3))
+    c2 = rng.normal(size=(n, 3))
+    c3 = rng.normal(size=(n, 3))
+    mass = rng.uniform(0.2, 1.0, size=n)
+    t0 = mp.mpf("0.29")
+
+    def pos(k, d, t):
+        return (mp.mpf(c0[k, d]) + mp.mpf(c1[k, d]) * t + mp.mpf(c2[k, d]) * t ** 2 / 2
+                + mp.mpf(c3[k, d]) * t ** 3 / 6)
+
+    def pair_acc(i, j, d, t):
+        r = [pos(j, e, t) - pos(i, e, t) for e in range(3)]
+        r2 = sum(x * x for x in r) + mp.mpf(eps) ** 2
+        return mp.mpf(mass[j]) * r[d] / r2 ** mp.mpf(1.5)
+
+    tf = float(t0)
+    xp = c0 + c1 * tf + c2 * tf ** 2 / 2 + c3 * tf ** 3 / 6
+    vp = c1 + c2 * tf + c3 * tf ** 2 / 2
+    ap = c2 + c3 * tf
+    sc = oracle.eval_absum(mass, xp, vp, ap, eps)
+    for i in range(n):
+        ref = np.zeros(3)
+        for j in range(n):
+            if j == i:
+                continue
+            for col, order in ((0, 0), (1, 1), (2, 2)):
+                vec = [mp.diff(lambda t: pair_acc(i, j, d, t), t0, order) if order else pair_acc(i, j, d, t0)
+                       for d in range(3)]
+                ref[col] += float(mp.sqrt(sum(x * x for x in vec)))
+        for col in range(3):
+            assert abs(sc[i, col] - ref[col]) <= 1e-12 * ref[col], (i, col, sc[i, col], ref[col])
+
+
 def test_eval_subset_equals_full_rows_and_skips_self():
     p = inputs.plummer(50, 3)
     ap = rng.normal(size=(50, 3))

@@ -31,6 +31,13 @@ PLANTED = [
     ("4th-order interpolation: crackle coefficient", "double c = (12.0 * (a0[k] - a1[k])", "double c = (10.0 * (a0[k] - a1[k])"),
     ("angular momentum component sign", "Lz += mass[i] * (r[0] * u[1] - r[1] * u[0]);",
      "Lz += mass[i] * (r[1] * u[0] - r[0] * u[1]);"),
+    ("condition scale: snap term loses -3 beta A",
+     "S[k] = mass[j] * a[k] / r3 - 6.0 * alpha * J[k] - 3.0 * beta * A[k];",
+     "S[k] = mass[j] * a[k] / r3 - 6.0 * alpha * J[k];"),
+    ("condition scale: sign of the jerk's alpha term", "J[k] = mass[j] * v[k] / r3 - 3.0 * alpha * A[k];",
+     "J[k] = mass[j] * v[k] / r3 + 3.0 * alpha * A[k];"),
+    ("condition scale: jerk and snap columns swapped", "out[3 * q + 1] = sj;\n        out[3 * q + 2] = ss;",
+     "out[3 * q + 1] = ss;\n        out[3 * q + 2] = sj;"),
 ]
 
 
