@@ -1,24 +1,32 @@
 #!/usr/bin/env python
 """Throughput benchmark of the Hermite block-step engine (acc/jerk/snap interactions/s).
 
-Default workload: the Plummer sphere of N = 65536 equal-mass particles in Henon
-units (seed 2), eps = 1e-4, eta = 0.45, dt_max = 1/16, integrated with power-of-
-two block time steps.  One step = advancing the system by one dt_max: every
-block step in that interval (next-block selection, FP64 prediction, evaluation,
-j-split reduction, FP64 correction with the time-step update) plus the energy
-at the synchronisation time that ends it.  value = sum over block steps of
-m * N (pair evaluations) per second of device time, mixed precision (FP32 pair
-arithmetic, double-single position differences, compensated sums, FP64 state).
+Default workload (the largest configuration, run on one GPU): a Plummer sphere
+of N = 8,388,608 particles with Salpeter masses on [0.1, 100] (seed 5), Henon
+units, eps = 1e-4, eta = 0.45, dt_max = 1/16, mixed precision (FP32 pair
+arithmetic in packed f32x2 instructions, double-single position differences,
+compensated sums, FP64 state, predictor, corrector and time steps).  The
+start-up (hg_init: every particle active at t = 0, 7.0e13 pair evaluations) is
+set-up, timed and reported apart.  One step = one graph-replayed block step
+(next-block selection fused into the FP64 prediction, evaluation, j-split
+reduction, FP64 correction with the new time steps); value = sum of m * N
+over the timed block steps per second of device time.  The energy (the
+paper's synchronisation-time diagnostic) is not part of a step: no
+synchronisation time (a multiple of dt_max) is reached within a few block steps
+at this N, and an FP64-pair energy of 2^23 particles costs tens of minutes.
 
-The line also carries the FP64 path on the same system over its first 1/8 time
-unit (the plain FP64 job) with both paths' |dE/E| there, the CPU oracle timed on
-a bounded sample, an end-to-end figure through the C ABI with host buffers, the
-evaluation kernel's roofline, sampled SM clocks and the kernel launch count.
-Inputs stay resident in HBM between steps; the FP64 state is 176 B/particle.
+Beside the line: the mixed kernel against the FP64 kernel on a seeded subset of
+4096 particles at this N (same state; errors and both kernels' rates); both
+paths integrated from t = 0 to 1/8 on the N = 65536 Plummer sphere with
+FP64-pair energies for both (|dE/E| of each, "mixed vs FP64 at stated
+|dE/E|"); the measured FP32 / FP64 FMA peaks; the CPU oracle on a bounded
+sample; an end-to-end figure through the C ABI with host buffers; the
+evaluation kernel's roofline; sampled SM clocks and the kernel launch count.
 
 --impl reference times the CPU oracle (plain single-threaded C) on a bounded
 sample of the same workload.  Under torchrun each rank runs its own replica
 (seed + rank) on its own GPU: weak scaling, no collective on the data path.
+--mode selects the other configurations (one JSON line each).
 """
 from __future__ import annotations
 
@@ -46,9 +54,19 @@ NUM_SMS = 152
 # kernel is unchanged.
 EVAL_TRAFFIC = {(65536, "equal", "mixed"): 3.48e6}
 
-
-def parse_defaults():
-    return {"n": 65536, "imf": "equal", "seed": 2, "t_end": 0.125}
+# Workload of each mode: (n, imf, seed, eps, t_end); explicit flags override.
+MODE_DEFAULTS = {
+    "headline": (1 << 23, "salpeter", 5, 1e-4, 0.125),
+    "interval": (65536, "equal", 2, 1e-4, 0.125),
+    "block-sizes": (65536, "equal", 2, 1e-4, 0.125),
+    "accuracy": (1 << 20, "salpeter", 3, 1e-4, 0.125),
+    "large": (1 << 23, "salpeter", 5, 1e-4, 0.125),
+    "eta-sweep": (16384, "equal", 2, 1e-4, 2.5),
+    "jsplit": (16384, "equal", 2, 1e-4, 0.125),
+    "batch": (0, "equal", 4, 1e-3, 0.125),
+}
+SUBSET = 4096          # particles of the mixed-vs-FP64 kernel comparison at the headline N
+ENERGY_JOB = dict(n=65536, imf="equal", seed=2, eps=1e-4, t_end=0.125)
 
 
 def parse():
@@ -57,43 +75,60 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=65536)
-    ap.add_argument("--imf", choices=["equal", "salpeter"], default="equal")
-    ap.add_argument("--eps", type=float, default=1e-4)
-    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--imf", choices=["equal", "salpeter"], default=None)
+    ap.add_argument("--eps", type=float, default=None)
+    ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--interval", type=float, default=1.0 / 16)
     ap.add_argument("--block-steps", type=int, default=0,
-                    help="if > 0, one step = this many block steps (no energy) instead of one interval")
+                    help="headline: block steps per step (default 1); interval: if > 0, one step = this many "
+                         "block steps (no energy) instead of one interval")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--batch", action="store_true",
                     help="independent-clusters workload: batched context vs one context per cluster")
     ap.add_argument("--clusters", type=int, default=512)
-    ap.add_argument("--t-end", type=float, default=0.125, help="block-sizes mode: integrate from 0 to this time")
+    ap.add_argument("--t-end", type=float, default=None, help="block-sizes mode: integrate from 0 to this time")
     ap.add_argument("--bh-mass", type=float, default=0.0,
                     help="block-sizes mode: add a central object of this mass (stars: total mass 1)")
     ap.add_argument("--order", type=int, choices=[4, 6], default=6,
                     help="integration order: 6 (the paper's scheme) or 4 (p = 4 criterion)")
     ap.add_argument("--precisions", default="fp64,mixed", help="block-sizes / eta-sweep modes: which paths")
-    ap.add_argument("--mode", choices=["interval", "batch", "block-sizes", "accuracy", "large", "eta-sweep"],
-                    default="interval",
-                    help="interval: the default line; batch: 512 clusters; block-sizes: evaluation time per "
-                         "block-size bucket, FP64 and mixed, N = 65536 to t = 1/8; accuracy: N = 2^20 Salpeter, "
-                         "mixed vs FP64 per block step and |dE/E| of both; large: N = 2^23 Salpeter, 32 block "
-                         "steps including the start-up evaluation; eta-sweep: energy and angular-momentum "
-                         "errors against eta (N = 16384, both paths)")
+    ap.add_argument("--mode", choices=list(MODE_DEFAULTS), default="headline",
+                    help="headline: the default line (N = 2^23 Salpeter, mixed, block steps); interval: N = 65536 "
+                         "Plummer, one 1/16 interval of block steps + energy per step; batch: 512 clusters; "
+                         "block-sizes: evaluation time per block-size bucket, FP64 and mixed, N = 65536 to t = 1/8; "
+                         "accuracy: N = 2^20 Salpeter, mixed vs FP64 per block step and |dE/E| of both; large: "
+                         "N = 2^23 Salpeter, 32 block steps including the start-up evaluation; eta-sweep: energy "
+                         "and angular-momentum errors against eta (N = 16384, both paths); jsplit: evaluation "
+                         "rate against m at N_j = 16384 with the j-split forced off and on (Sect. 5.5 Bfactor)")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the cost model's launch plans (no hg_tune before the warm-up)")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.batch:
+        a.mode = "batch"
+    n, imf, seed, eps, t_end = MODE_DEFAULTS[a.mode]
+    a.n = n if a.n is None else a.n
+    a.imf = imf if a.imf is None else a.imf
+    a.seed = seed if a.seed is None else a.seed
+    a.eps = eps if a.eps is None else a.eps
+    a.t_end = t_end if a.t_end is None else a.t_end
+    return a
 
 
 def workload_name(a):
-    step = (f"{a.block_steps} block steps" if a.block_steps > 0 else
-            f"one {a.interval:g} time-unit interval of block steps + energy at its end")
-    return (f"Plummer N={a.n} Henon units, {a.imf} masses (seed {a.seed}), eps={a.eps:g}, eta=0.45, "
-            f"dt_max=1/16, power-of-two block steps; step = {step}")
+    if a.mode == "headline":
+        step = (f"{a.block_steps or 1} graph-replayed block step(s) (select+predict, evaluate, reduce, correct); "
+                f"start-up evaluation before the warm-up")
+    elif a.block_steps > 0:
+        step = f"{a.block_steps} block steps"
+    else:
+        step = f"one {a.interval:g} time-unit interval of block steps + energy at its end"
+    masses = "Salpeter masses 0.1-100" if a.imf == "salpeter" else "equal masses"
+    return (f"Plummer N={a.n} Henon units, {masses} (seed {a.seed}), eps={a.eps:g}, eta=0.45, "
+            f"dt_max=1/16, power-of-two block steps, mixed precision; step = {step}")
 
 
 def sm_max_mhz():
@@ -195,9 +230,11 @@ def oracle_sample_size(n, target_interactions=6e8):
 def cpu_baseline(p, eps):
     m = oracle_sample_size(p.n)
     inter, sec = oracle_sample_step(p, m, eps, 1.0 / 64)
-    return {"value": inter / sec, "unit": "interactions/s", "cores": 1, "kind": "oracle",
+    return {"value": inter / sec, "unit": "interactions/s", "cores": 1, "host_cores": os.cpu_count(),
+            "kind": "oracle",
             "sample": f"one oracle block step with {m} of N={p.n} active (predict all N, evaluate {m}xN, "
-                      f"correct {m}): {sec:.1f} s of single-threaded C FP64"}
+                      f"correct {m}): {sec:.1f} s of single-threaded C FP64 on 1 of the host's "
+                      f"{os.cpu_count()} cores"}
 
 
 def run_reference(a, rank):
@@ -218,9 +255,12 @@ def run_reference(a, rank):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "interactions/s", "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot_s / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(a), "sample": f"each step: oracle block step, {m} of N active"},
-        "cpu_baseline": {"value": v, "unit": "interactions/s", "cores": 1, "kind": "oracle",
-                         "sample": f"each step: oracle block step with {m} of N={a.n} active"},
+        "config": {"workload": workload_name(a), "n": a.n,
+                   "sample": f"each step: oracle block step, {m} of N active"},
+        "cpu_baseline": {"value": v, "unit": "interactions/s", "cores": 1, "host_cores": os.cpu_count(),
+                         "kind": "oracle",
+                         "sample": f"each step: oracle block step with {m} of N={a.n} active (predict all N, "
+                                   f"evaluate {m}xN, correct {m}), single-threaded C FP64"},
         "e2e": {"value": v, "unit": "interactions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -263,18 +303,44 @@ def tune(hg, ctx, a):
                         for e in rep if e["chosen"] >= 0]}
 
 
-def roofline(hg, inter, prof, mixed, mhz, kind, traffic=None):
+def roofline(hg, inter, prof, mixed, mhz, kind, traffic=None, measured=None):
+    """Roofline of the evaluation kernel: algorithmic flops (pairs x 77) over the
+    evaluation section's CUDA-event time, against the FMA-pipe peak derived from
+    unit counts and the maximum clock, and (when given) against the peak the
+    library's FMA microbenchmark measured on this GPU."""
     eval_s = prof["ms"]["evaluate"] / 1e3
     peak = fp32_peak_tflops(mhz) if mixed else fp64_peak_tflops(mhz)
     flops = FLOPS_F32 if mixed else FLOPS_F64
     ach = inter * flops / eval_s / 1e12 if eval_s > 0 else None
-    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": (ach / peak) if ach else None, "traffic": traffic,
-            "kernel": "k_eval<Mixed>" if mixed else "k_eval<F64>",
-            "flops_per_interaction": flops,
-            "peak_note": ((f"FP32 FMA pipe: {NUM_SMS} SMs x 128 lanes x 2 flops" if mixed else
-                           f"FP64 pipe: {NUM_SMS} SMs x 2 DFMA x 2 flops") + f" x {mhz:.0f} MHz ({kind} max clock)"),
-            "eval_share_of_step": eval_s / (sum(prof["ms"].values()) / 1e3) if prof["ms"] else None}
+    out = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+           "frac": (ach / peak) if ach else None, "traffic": traffic,
+           "kernel": "k_eval<Mixed>" if mixed else "k_eval<F64>",
+           "flops_per_interaction": flops,
+           "flops_per_interaction_rsqrt_as_4": flops + 4,
+           "paper_flops_per_interaction": PAPER_FLOPS,
+           "peak_note": ((f"FP32 FMA pipe: {NUM_SMS} SMs x 128 lanes x 2 flops" if mixed else
+                          f"FP64 pipe: {NUM_SMS} SMs x 2 DFMA x 2 flops") + f" x {mhz:.0f} MHz ({kind} max clock)"),
+           "eval_share_of_step": eval_s / (sum(prof["ms"].values()) / 1e3) if prof["ms"] else None}
+    if measured:
+        mp = max(measured.get("f32", 0.0), measured.get("f32x2", 0.0)) if mixed else measured.get("f64", 0.0)
+        if mp > 0 and ach:
+            out["measured_peak"] = mp
+            out["frac_of_measured"] = ach / mp
+            out["measured_peak_note"] = ("FMA microbenchmark on this GPU (hg_peak_flops: every SM full, 8 "
+                                         "independent chains per thread, CUDA events), best of scalar and packed "
+                                         "FP32" if mixed else "FMA microbenchmark on this GPU (hg_peak_flops, DFMA)")
+    return out
+
+
+def measure_peaks(hg, device, stream):
+    """FMA rates of the CUDA cores measured by the library (TFLOP/s)."""
+    out = {}
+    for form in ("f32", "f32x2", "f64"):
+        try:
+            out[form] = hg.hg_peak_flops(form, device, stream)[0]
+        except Exception as e:    # reported, never fatal to the line
+            out[form + "_error"] = str(e)
+    return out
 
 
 def aggregate(ms, interactions, dist, device):
@@ -290,7 +356,261 @@ def aggregate(ms, interactions, dist, device):
     return float(t.item()), int(c.item())
 
 
-def run_ours(a, rank, world, dist):
+def run_headline(a, rank, world, dist):
+    """The default line: N = 2^23 Salpeter Plummer sphere, mixed precision,
+    graph-replayed block steps timed one step at a time."""
+    import torch
+    from paper_1207_2367_gb300 import binding as hg
+    from paper_1207_2367_gb300 import inputs
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    hg.load()
+    stream = torch.cuda.Stream()
+    bs = a.block_steps or 1
+    peaks = measure_peaks(hg, local, stream) if rank == 0 else None
+    p = inputs.plummer(a.n, a.seed + rank, imf=a.imf)
+    # The context times its sections with CUDA events (profile = 1): a few us
+    # per block step against ~1 s of evaluation at this N.
+    opts = hg.hg_default_opts(precision=hg.HG_MIXED, energy_precision=hg.HG_MIXED, dt_max=1.0 / 16,
+                              device=local, profile=1, stream=stream)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    ctx = hg.hg_init(p.mass, p.pos, p.vel, a.eps, 0.45, opts)
+    startup_s = time.perf_counter() - w0
+    try:
+        tuning = tune(hg, ctx, a)
+        for _ in range(a.warmup):
+            hg.hg_step(ctx, bs)
+        hg.hg_get_stats(ctx)
+
+        def barrier():
+            if dist is not None:
+                dist.barrier()
+
+        s0 = hg.hg_get_stats(ctx)
+        hg.hg_get_profile(ctx, reset=True)
+        clocks = Clocks(local)
+        barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        ms, per_step = 0.0, []
+        torch.cuda.nvtx.range_push("timed")      # ncu --nvtx --nvtx-include "timed/" profiles only these launches
+        for _ in range(a.steps):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            hg.hg_step(ctx, bs)
+            ev1.record(stream)
+            ev1.synchronize()
+            per_step.append(ev0.elapsed_time(ev1))
+            ms += per_step[-1]
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        clk = clocks.stop()
+        barrier()
+        s1 = hg.hg_get_stats(ctx)
+        prof = hg.hg_get_profile(ctx)
+        inter = s1["interactions"] - s0["interactions"]
+        launches = s1["kernels"] - s0["kernels"]
+        steps_taken = s1["block_steps"] - s0["block_steps"]
+        ms_max, inter_tot = aggregate(ms, inter, dist, "cuda")
+        value = inter_tot / (ms_max / 1e3)
+        mhz, kind = sm_max_mhz()
+        roof = roofline(hg, inter, prof, True, mhz, kind, EVAL_TRAFFIC.get((a.n, a.imf, "mixed")), peaks)
+        roof["eval_ms_per_launch"] = prof["ms"]["evaluate"] / max(1, prof["block_steps"])
+        roof["pairs_per_launch"] = inter / max(1, steps_taken)
+        e2e = run_e2e_blocks(a, hg, ctx, bs) if (not a.no_e2e and rank == 0) else None
+        subset = subset_vs_fp64(hg, ctx, p, a, stream, local) if (not a.no_fp64 and rank == 0) else None
+    finally:
+        hg.hg_free(ctx)
+    energy = energy_comparison(hg, stream, local) if (not a.no_fp64 and rank == 0) else None
+    cpu = cpu_baseline(p, a.eps) if (not a.no_cpu_baseline and rank == 0) else None
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": "interactions/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(a), "n": a.n, "imf": a.imf, "seed": a.seed, "eps": a.eps,
+                   "block_steps_per_step": bs,
+                   "precision": "mixed: f32 pair arithmetic (packed f32x2, two pairs per instruction), "
+                                "double-single dr, Kahan f32 sums widened to f64, f64 state/predictor/corrector",
+                   "l2": "not flushed: the working set (436 MB of j-records streamed by every i-tile, 1.5 GB "
+                         "of FP64 state) is larger than L2 (129 MB); inputs resident in HBM",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": int(launches),
+        "block_steps": steps_taken,
+        "interactions": inter,
+        "mean_block_size": inter / max(1, steps_taken) / a.n,
+        "ms_per_step_each": per_step,
+        "startup": {"seconds": startup_s, "interactions": a.n * a.n,
+                    "rate": a.n * a.n / startup_s,
+                    "note": "hg_init wall time: upload, validation, evaluation with all N active, first steps"},
+        "gflops_paper_convention": value * PAPER_FLOPS / 1e9,
+        "sections_ms": prof["ms"],
+        "peaks_measured_tflops": peaks,
+        "tuning": tuning,
+        "mixed_vs_fp64": {"subset_at_n": subset, "energy_job": energy},
+    }), flush=True)
+
+
+def run_e2e_blocks(a, hg, ctx, bs):
+    """The headline metric through the public C ABI with host buffers: every step
+    uploads the whole state from pinned host memory (hg_set_state), takes the
+    block step(s) (hg_step) and reads the whole state back (hg_get_state)."""
+    import torch
+    n = a.n
+    host = {f: torch.empty((n,) if f in ("mass", "t", "dt") else (n, 3), dtype=torch.float64).pin_memory()
+            for f in hg.STATE_FIELDS}
+    t_sys = hg.hg_get_state(ctx, host)
+    nbytes = sum(h.numel() * 8 for h in host.values())
+    s0 = hg.hg_get_stats(ctx)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(a.steps):
+        hg.hg_set_state(ctx, host, t_sys)
+        hg.hg_step(ctx, bs)
+        t_sys = hg.hg_get_state(ctx, host)
+    wall = time.perf_counter() - w0
+    inter = hg.hg_get_stats(ctx)["interactions"] - s0["interactions"]
+    return {"value": inter / wall, "unit": "interactions/s", "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes, "wall_s": wall, "steps": a.steps,
+            "note": "host wall clock; per step: hg_set_state from pinned host memory, hg_step, hg_get_state"}
+
+
+def subset_vs_fp64(hg, ctx, p, a, stream, device):
+    """The mixed kernel against the FP64 kernel on the same state: a seeded
+    subset of SUBSET particles (numpy default_rng(6)) of the mixed context's
+    current state, both predicted 2^-20 past its last block time.  Also each
+    kernel's device time and rate on that evaluation."""
+    import torch
+    n = a.n
+    rng = np.random.default_rng(6)
+    lst = np.sort(rng.choice(n, SUBSET, replace=False)).astype(np.int32)
+    lst_d = torch.tensor(lst, device="cuda")
+    dst, t_sys = _device_state(hg, ctx, n)
+    ref = hg.hg_init(p.mass, p.pos, p.vel, a.eps, 0.45,
+                     hg.hg_default_opts(precision=hg.HG_FP64, dt_max=1.0 / 16, stream=stream, device=device,
+                                        start_mode=1))
+    try:
+        hg.hg_set_state(ref, dst, t_sys)
+        del dst
+        t = t_sys + 2.0 ** -20
+        got = [np.empty((SUBSET, 3)) for _ in range(3)]
+        want = [np.empty((SUBSET, 3)) for _ in range(3)]
+        hg.hg_predict(ctx, t)
+        us_mixed = hg.hg_time_evaluate(ctx, lst_d, SUBSET, 3)
+        hg.hg_evaluate(ctx, lst, SUBSET, *got)
+        hg.hg_predict(ref, t)
+        us_f64 = hg.hg_time_evaluate(ref, lst_d, SUBSET, 1)
+        hg.hg_evaluate(ref, lst, SUBSET, *want)
+    finally:
+        hg.hg_free(ref)
+    pairs = SUBSET * n
+    return {"subset": f"{SUBSET} particles (numpy default_rng(6) choice), predicted 2^-20 past the last block "
+                      f"time t = {t_sys!r}",
+            "errors_vs_fp64_kernel": {name: _rel_stats(g, w) for name, g, w in
+                                      zip(("acc", "jerk", "snap"), got, want)},
+            "tolerance_normwise": {"acc": 1e-6, "jerk": 1e-5, "snap": 1e-4},
+            "mixed_rate": pairs / (us_mixed * 1e-6), "fp64_rate": pairs / (us_f64 * 1e-6),
+            "mixed_over_fp64": us_f64 / us_mixed, "unit": "interactions/s (evaluation + reduction kernels)"}
+
+
+def energy_comparison(hg, stream, device):
+    """Mixed vs FP64 at the same job: both paths integrate the N = 65536 Plummer
+    sphere (equal masses, seed 2, eps 1e-4, eta 0.45, dt_max 1/16) from t = 0 to
+    1/8 with the cost model's plans; energies of both with FP64 pair arithmetic;
+    device time of the block steps (CUDA events) for the rate."""
+    import torch
+    from paper_1207_2367_gb300 import inputs
+    j = ENERGY_JOB
+    p = inputs.plummer(j["n"], j["seed"], imf=j["imf"])
+    out = {"workload": f"Plummer N={j['n']}, {j['imf']} masses (seed {j['seed']}), eps={j['eps']:g}, eta=0.45, "
+                       f"dt_max=1/16, t = 0 -> {j['t_end']:g}; FP64-pair energies for both paths"}
+    for name, prec in (("mixed", hg.HG_MIXED), ("fp64", hg.HG_FP64)):
+        o = hg.hg_default_opts(precision=prec, energy_precision=hg.HG_FP64, dt_max=1.0 / 16, stream=stream,
+                               device=device)
+        ctx = hg.hg_init(p.mass, p.pos, p.vel, j["eps"], 0.45, o)
+        try:
+            E0 = sum(hg.hg_energy(ctx))
+            L0 = hg.hg_angular_momentum(ctx)
+            s0 = hg.hg_get_stats(ctx)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            hg.hg_advance(ctx, j["t_end"])
+            ev1.record(stream)
+            ev1.synchronize()
+            sec = ev0.elapsed_time(ev1) / 1e3
+            s1 = hg.hg_get_stats(ctx)
+            E1 = sum(hg.hg_energy(ctx))
+            L1 = hg.hg_angular_momentum(ctx)
+            inter = s1["interactions"] - s0["interactions"]
+            out[name] = {"dE_over_E": abs((E1 - E0) / E0), "E0": E0, "t": s1["t_sys"],
+                         "dL": float(np.linalg.norm(L1 - L0)), "block_steps": s1["block_steps"] - s0["block_steps"],
+                         "interactions": inter, "seconds": sec, "value": inter / sec, "unit": "interactions/s"}
+        finally:
+            hg.hg_free(ctx)
+    out["rate_mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    out["dE_mixed_over_fp64"] = out["mixed"]["dE_over_E"] / out["fp64"]["dE_over_E"]
+    return out
+
+
+def run_jsplit(a):
+    """Sect. 5.5 Bfactor comparison: evaluation rate against the block size m at
+    N_j = --n (default 16384, equal-mass Plummer, seed 2) with the j-split forced
+    off (opts.jsplit = 1: one j-chunk per i-tile) against the cost model's plan
+    and the autotuned plan, both precisions; evaluation + reduction kernels timed
+    with CUDA events (hg_time_evaluate).  m = 1, 2, 4, ..., N_j; each list is
+    spread evenly over the particles."""
+    import torch
+    from paper_1207_2367_gb300 import binding as hg
+    from paper_1207_2367_gb300 import inputs
+
+    torch.cuda.set_device(0)
+    hg.load()
+    stream = torch.cuda.Stream()
+    n = a.n
+    p = inputs.plummer(n, a.seed, imf=a.imf)
+    ms = []
+    m = 1
+    while m <= n:
+        ms.append(m)
+        m *= 2
+    out = {"metric": "evaluation rate against block size, j-split off / cost model / tuned", "unit": "interactions/s",
+           "config": {"workload": f"Plummer N={n}, {a.imf} masses (seed {a.seed}), eps={a.eps:g}, start-up state, "
+                                  "lists spread evenly, evaluation + reduction timed (hg_time_evaluate)"}}
+    wanted = {"fp64": hg.HG_FP64, "mixed": hg.HG_MIXED}
+    for name in [x for x in a.precisions.split(",") if x]:
+        rows = {}
+        for arm, jsplit in (("no_jsplit", 1), ("cost_model", 0), ("tuned", 0)):
+            o = hg.hg_default_opts(precision=wanted[name], dt_max=1.0 / 16, stream=stream, jsplit=jsplit)
+            ctx = hg.hg_init(p.mass, p.pos, p.vel, a.eps, 0.45, o)
+            try:
+                if arm == "tuned":
+                    hg.hg_tune(ctx, m_max=n)
+                hg.hg_predict(ctx, 0.0)
+                for m in ms:
+                    lst = np.unique(np.linspace(0, n - 1, m).astype(np.int32))
+                    us = hg.hg_time_evaluate(ctx, lst, lst.shape[0], 0)
+                    rows.setdefault(m, {})[arm] = {"us": us, "rate": lst.shape[0] * n / (us * 1e-6)}
+            finally:
+                hg.hg_free(ctx)
+        table = []
+        for m in ms:
+            r = rows[m]
+            table.append({"m": m, **{k: r[k] for k in r},
+                          "gain_cost_model": r["no_jsplit"]["us"] / r["cost_model"]["us"],
+                          "gain_tuned": r["no_jsplit"]["us"] / r["tuned"]["us"]})
+        out[name] = table
+    print(json.dumps(out), flush=True)
+
+
+def run_interval(a, rank, world, dist):
     import torch
     from paper_1207_2367_gb300 import binding as hg
     from paper_1207_2367_gb300 import inputs
@@ -370,7 +690,7 @@ def run_ours(a, rank, world, dist):
     prof = hg.hg_get_profile(pctx)
     prof_inter = hg.hg_get_stats(pctx)["interactions"] - q0["interactions"]
     hg.hg_free(pctx)
-    fp64 = run_fp64_job(a, hg, p, stream, local, mhz, kind) if (mixed and not a.no_fp64 and rank == 0) else None
+    fp64 = energy_comparison(hg, stream, local) if (mixed and not a.no_fp64 and rank == 0) else None
     cpu = cpu_baseline(p, a.eps) if (not a.no_cpu_baseline and rank == 0) else None
     if rank != 0:
         return
@@ -397,7 +717,7 @@ def run_ours(a, rank, world, dist):
         "gflops_paper_convention": value * PAPER_FLOPS / 1e9,
         "sections_ms": prof["ms"],
         "tuning": tuning,
-        "fp64": fp64,
+        "mixed_vs_fp64": fp64,
     }
     print(json.dumps(out), flush=True)
 
@@ -422,38 +742,6 @@ def run_e2e(a, hg, ctx, stream, run):
     inter = hg.hg_get_stats(ctx)["interactions"] - s0["interactions"]
     return {"value": inter / wall, "unit": "interactions/s", "h2d_bytes_per_step": nbytes,
             "d2h_bytes_per_step": nbytes + (16 if a.block_steps == 0 else 0), "wall_s": wall}
-
-
-def run_fp64_job(a, hg, p, stream, device, mhz, kind):
-    """The plain FP64 path on the same system from t = 0 to 1/8 (two dt_max
-    intervals, energy at each end), timed as a whole job."""
-    import torch
-    ctx = make_ctx(hg, p, a, hg.HG_FP64, stream, device)
-    try:
-        tuning = tune(hg, ctx, a)
-        K0, W0 = hg.hg_energy(ctx)
-        s0 = hg.hg_get_stats(ctx)
-        hg.hg_get_profile(ctx, reset=True)
-        torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        for k in (1, 2):
-            hg.hg_advance(ctx, k / 16)
-            K1, W1 = hg.hg_energy(ctx)
-        ev1.record(stream)
-        ev1.synchronize()
-        ms = ev0.elapsed_time(ev1)
-        s1 = hg.hg_get_stats(ctx)
-        prof = hg.hg_get_profile(ctx)
-        inter = s1["interactions"] - s0["interactions"]
-        return {"workload": "same system, t = 0 to 0.125 (two 1/16 steps, energy at each end)",
-                "value": inter / (ms / 1e3), "unit": "interactions/s", "ms_total": ms,
-                "block_steps": s1["block_steps"] - s0["block_steps"],
-                "dE_over_E_t_0.125": abs((K1 + W1 - K0 - W0) / (K0 + W0)),
-                "roofline": roofline(hg, inter, prof, False, mhz, kind), "sections_ms": prof["ms"],
-                "tuning": tuning}
-    finally:
-        hg.hg_free(ctx)
 
 
 def run_batch(a):
@@ -814,18 +1102,9 @@ def run_large(a):
 
 def main():
     a = parse()
-    if a.batch or a.mode == "batch":
-        run_batch(a)
-        return
-    modes = {"block-sizes": run_block_sizes, "accuracy": run_accuracy, "large": run_large,
-             "eta-sweep": run_eta_sweep}
-    if a.mode in modes:
-        defaults = {"accuracy": dict(n=1 << 20, imf="salpeter", seed=3),
-                    "large": dict(n=1 << 23, imf="salpeter", seed=5),
-                    "eta-sweep": dict(n=16384, t_end=2.5)}.get(a.mode, {})
-        for k, v in defaults.items():
-            if getattr(a, k) == parse_defaults()[k]:
-                setattr(a, k, v)
+    modes = {"batch": run_batch, "block-sizes": run_block_sizes, "accuracy": run_accuracy, "large": run_large,
+             "eta-sweep": run_eta_sweep, "jsplit": run_jsplit}
+    if a.mode in modes and a.impl == "ours":
         modes[a.mode](a)
         return
     rank = int(os.environ.get("RANK", "0"))
@@ -841,7 +1120,7 @@ def main():
         td.init_process_group("nccl")
         dist = td
     try:
-        run_ours(a, rank, world, dist)
+        (run_interval if a.mode == "interval" else run_headline)(a, rank, world, dist)
     finally:
         if dist is not None:
             dist.destroy_process_group()

@@ -232,16 +232,34 @@ const char *hg_init_error(void);
  *   eps        softening >= 0; precision HG_FP64 or HG_MIXED;
  *   idx        [m] device int32, strictly increasing, in [0, n) (HG_EINVAL otherwise);
  *   acc, jerk, snap  [m][3] FP64 device outputs; stream  cudaStream_t or NULL.
- * Its scratch is one fixed array of about 6 MB in the library's device memory,
- * present on every GPU that loads the library until the process exits.  The
- * first call on a device looks up that array's address (make it before any
- * stream capture on that device).  Every call shares the array, so calls whose
- * work overlaps on the GPU (different streams or threads) race; the call
- * synchronizes its stream before returning.  Errors as hg_evaluate, message in
- * hg_init_error(). */
+ * Its scratch is one fixed array of about 6.5 MB in the library's device
+ * memory, kept on a device until the process exits once it is there.  The
+ * first call on a device (any m) looks up that array's address; under CUDA's
+ * default lazy module loading that first call is also when the driver loads
+ * the array onto the device, i.e. allocates its 6.5 MB (set
+ * CUDA_MODULE_LOADING=EAGER to have it allocated when the library is loaded
+ * instead).  A call with m = 0 does only this set-up: make one at start-up,
+ * before any stream capture on that device, so that later calls allocate
+ * nothing.  Every call shares the array, so calls whose work overlaps on the
+ * GPU (different streams or threads) race; the call synchronizes its stream
+ * before returning.  Errors as hg_evaluate, message in hg_init_error(). */
 int hg_evaluate_static(int64_t n, const double *mass, const double *pos, const double *vel, const double *acc_pred,
                        double eps, int32_t precision, const int32_t *idx, int64_t m, double *acc, double *jerk,
                        double *snap, void *stream);
+
+/* Measured arithmetic peak of the CUDA cores of `device`, the denominator of
+ * the evaluation kernels' roofline (the paper derives its peaks from unit
+ * counts and clock, Sect. 5.7 and Table 2; this measures them).  form: 0 =
+ * scalar FP32 FMA, 1 = packed FP32 FMA (fma.rn.f32x2, the mixed evaluation's
+ * form), 2 = FP64 FMA.  Every SM is filled with threads that each advance 8
+ * independent FMA chains; one warm-up launch, then one launch timed with CUDA
+ * events on `stream` (cudaStream_t or NULL).  *tflops receives the FMA rate in
+ * TFLOP/s (2 flops per FMA and lane), *ms (may be NULL) the timed launch's
+ * duration.  Changes no device setting (clocks stay as they are: the figure is
+ * taken at whatever clock the GPU runs).  Allocates 16 bytes for the duration
+ * of the call.  Errors: HG_EINVAL (form, device), HG_ECUDA; message in
+ * hg_init_error().  Synchronizes. */
+int hg_peak_flops(int32_t form, int32_t device, void *stream, double *tflops, double *ms);
 
 /* ------------------------------------------------------------------------
  * Autotuning of the evaluation's launch plan (the paper's "Bfactor", Sect. 3:
@@ -289,12 +307,40 @@ typedef struct hg_tune_entry {
  * Errors: HG_EINVAL, HG_ECUDA, HG_ETIMEOUT.  Synchronizes. */
 int hg_tune(hg_ctx *ctx, int64_t m_max, int32_t reps, hg_tune_entry *report, int32_t cap, int32_t *n_out);
 
+/* Device time of one evaluation (evaluation and j-split reduction kernels,
+ * with the launch plan the context would choose for m: tuning table, else cost
+ * model, subject to opts.tpi / opts.jsplit) of the m listed particles (idx
+ * strictly increasing, in range, host or device) against the data of the last
+ * hg_predict: one warm-up launch, then reps launches (0: automatic, ~2 ms
+ * worth, 3 to 64) timed with CUDA events on the context's stream; *us receives
+ * the mean in microseconds.  The integration state is unchanged; the results
+ * are not kept (a pending hg_evaluate is dropped, the prediction stays).  The
+ * measurement the tuner makes, offered for benchmarks such as the paper's
+ * Bfactor comparison (Sect. 5.5).  Errors: HG_EINVAL, HG_ESTATE (no
+ * prediction), HG_ECUDA, HG_ETIMEOUT.  Synchronizes. */
+int hg_time_evaluate(hg_ctx *ctx, const int32_t *idx, int64_t m, int32_t reps, double *us);
+
 /* Copy the tuning table out / replace it (HG_TUNE_BUCKETS int16 values, host
  * memory; -1 entries use the cost model).  hg_set_tuning checks every value for
  * the context's kind (HG_EINVAL otherwise), so a table saved from one context
  * can be given to another of the same precision and kind on the same GPU model. */
 int hg_get_tuning(hg_ctx *ctx, int16_t *table);
 int hg_set_tuning(hg_ctx *ctx, const int16_t *table);
+
+/* Host-side fault injection, for testing the failure paths without a device
+ * fault (the library convenience has no counterpart in the paper).  After
+ * hg_inject_fault(HG_FAULT_ALLOC, n) the n-th device allocation the library
+ * makes for a context fails as if cudaMalloc had (the call returns HG_ENOMEM);
+ * after hg_inject_fault(HG_FAULT_CUDA, n) the n-th CUDA runtime call a
+ * context-based call checks fails without being made (HG_ECUDA, message
+ * "injected fault").  One fault, then the injector disarms itself;
+ * HG_FAULT_NONE disarms it.  Process-wide, counted across threads.  The
+ * environment variable HG_FAULT=alloc:<n> or HG_FAULT=cuda:<n> arms it when
+ * the library is loaded.  Errors: HG_EINVAL (kind, or n < 1). */
+#define HG_FAULT_NONE 0
+#define HG_FAULT_ALLOC 1
+#define HG_FAULT_CUDA 2
+int hg_inject_fault(int32_t kind, int64_t nth);
 
 /* Release the context and its device memory.  NULL is allowed. */
 void hg_free(hg_ctx *ctx);

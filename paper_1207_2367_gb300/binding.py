@@ -18,6 +18,7 @@ from . import _build
 
 HG_OK, HG_EINVAL, HG_ENOMEM, HG_ECUDA, HG_ESTATE, HG_ETIMEOUT = range(6)
 HG_FP64, HG_MIXED = 0, 1
+HG_FAULT_NONE, HG_FAULT_ALLOC, HG_FAULT_CUDA = 0, 1, 2
 _NAMES = {1: "HG_EINVAL", 2: "HG_ENOMEM", 3: "HG_ECUDA", 4: "HG_ESTATE", 5: "HG_ETIMEOUT"}
 
 
@@ -100,14 +101,19 @@ def load(path: str | None = None):
         L.hg_free.restype = None
         L.hg_evaluate_static.argtypes = [I64, P, P, P, P, D, C.c_int32, I32P, I64, P, P, P, P]
         L.hg_evaluate_static.restype = C.c_int
+        L.hg_peak_flops.argtypes = [C.c_int32, C.c_int32, P, C.POINTER(D), C.POINTER(D)]
+        L.hg_peak_flops.restype = C.c_int
         L.hg_angular_momentum.argtypes = [P, C.POINTER(D)]
         L.hg_bind_device.argtypes = [P, C.c_void_p, C.c_int]
         L.hg_tune.argtypes = [P, I64, C.c_int32, C.POINTER(hg_tune_entry), C.c_int32, C.POINTER(C.c_int32)]
+        L.hg_time_evaluate.argtypes = [P, I32P, I64, C.c_int32, C.POINTER(D)]
+        L.hg_inject_fault.argtypes = [C.c_int32, I64]
+        L.hg_inject_fault.restype = C.c_int
         L.hg_get_tuning.argtypes = [P, C.POINTER(C.c_int16)]
         L.hg_set_tuning.argtypes = [P, C.POINTER(C.c_int16)]
         for name in ("hg_init", "hg_next_block", "hg_predict", "hg_evaluate", "hg_correct", "hg_step",
                      "hg_advance", "hg_energy", "hg_get_state", "hg_set_state", "hg_get_stats", "hg_get_profile",
-                     "hg_tune", "hg_get_tuning", "hg_set_tuning", "hg_angular_momentum", "hg_bind_device"):
+                     "hg_tune", "hg_time_evaluate", "hg_get_tuning", "hg_set_tuning", "hg_angular_momentum", "hg_bind_device"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -265,6 +271,13 @@ def hg_tune(ctx, m_max=0, reps=0):
     return [{k: getattr(rep[q], k) for k in keys} for q in range(n.value)]
 
 
+def hg_time_evaluate(ctx, idx, m, reps=0):
+    """Mean device time (us) of evaluating the listed particles with the context's plan."""
+    us = C.c_double()
+    _check(ctx, load().hg_time_evaluate(ctx, _ptr(idx, np.int32), int(m), int(reps), C.byref(us)))
+    return us.value
+
+
 def hg_get_tuning(ctx):
     t = np.empty(HG_TUNE_BUCKETS, dtype=np.int16)
     _check(ctx, load().hg_get_tuning(ctx, t.ctypes.data_as(C.POINTER(C.c_int16))))
@@ -286,6 +299,28 @@ def hg_evaluate_static(mass, pos, vel, acc_pred, eps, precision, idx, m, acc, je
                                    _ptr(jerk), _ptr(snap), s)
     if rc != HG_OK:
         raise HGError(rc, load().hg_init_error().decode())
+
+
+PEAK_FORMS = {"f32": 0, "f32x2": 1, "f64": 2}
+
+
+def hg_peak_flops(form, device=0, stream=None):
+    """Measured FMA rate of the CUDA cores (form "f32", "f32x2" or "f64"):
+    (TFLOP/s, duration of the timed launch in ms)."""
+    s = getattr(stream, "cuda_stream", stream)
+    tf, ms = C.c_double(), C.c_double()
+    rc = load().hg_peak_flops(PEAK_FORMS[form], int(device), s, C.byref(tf), C.byref(ms))
+    if rc != HG_OK:
+        raise HGError(rc, load().hg_init_error().decode())
+    return tf.value, ms.value
+
+
+def hg_inject_fault(kind, nth=0):
+    """Testing: make the nth library allocation (HG_FAULT_ALLOC) or checked CUDA
+    call (HG_FAULT_CUDA) fail; HG_FAULT_NONE disarms."""
+    rc = load().hg_inject_fault(int(kind), int(nth))
+    if rc != HG_OK:
+        raise HGError(rc, "bad fault kind or count")
 
 
 def hg_size(ctx):

@@ -7,7 +7,10 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <string>
 #include <vector>
@@ -70,10 +73,49 @@ int fail(hg_ctx *c, int code, const std::string &msg)
     return code;
 }
 
+// ---------------------------------------------------------------------------
+// Host-side fault injection (testing): the nth device allocation or checked
+// CUDA call after arming fails as if the CUDA runtime had refused it, without
+// making the call.  Armed by hg_inject_fault or, at load, by the environment
+// variable HG_FAULT=alloc:<n> or HG_FAULT=cuda:<n>.  Process-wide.
+// ---------------------------------------------------------------------------
+std::atomic<int32_t> g_fault_kind{HG_FAULT_NONE};
+std::atomic<int64_t> g_fault_left{0};
+
+// True for the armed fault point (which disarms the injector).
+bool fault_point(int32_t kind)
+{
+    if (g_fault_kind.load(std::memory_order_relaxed) != kind) return false;
+    if (g_fault_left.fetch_sub(1) != 1) return false;
+    g_fault_kind.store(HG_FAULT_NONE);
+    return true;
+}
+
+struct FaultFromEnv {
+    FaultFromEnv()
+    {
+        const char *s = getenv("HG_FAULT");
+        if (!s) return;
+        const int32_t kind = strncmp(s, "alloc:", 6) == 0 ? HG_FAULT_ALLOC
+                             : strncmp(s, "cuda:", 5) == 0 ? HG_FAULT_CUDA
+                                                           : HG_FAULT_NONE;
+        const long long nth = kind == HG_FAULT_NONE ? 0 : atoll(strchr(s, ':') + 1);
+        if (nth > 0) {
+            g_fault_left.store(nth);
+            g_fault_kind.store(kind);
+        }
+    }
+} g_fault_from_env;
+
+constexpr cudaError_t kInjected = cudaErrorUnknown;
+
 #define HG_CUDA(ctx, call)                                                                        \
     do {                                                                                          \
-        cudaError_t e_ = (call);                                                                  \
-        if (e_ != cudaSuccess) return fail((ctx), HG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        const bool inj_ = fault_point(HG_FAULT_CUDA);                                             \
+        cudaError_t e_ = inj_ ? kInjected : (call);                                               \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail((ctx), HG_ECUDA,                                                          \
+                        std::string(#call) + ": " + (inj_ ? "injected fault" : cudaGetErrorString(e_))); \
     } while (0)
 
 bool is_pow2(double x)
@@ -97,6 +139,7 @@ T *dalloc(hg_ctx *c, int64_t count)
 {
     void *p = nullptr;
     if (count < 1) count = 1;
+    if (fault_point(HG_FAULT_ALLOC)) return nullptr;
     if (cudaMalloc(&p, (size_t)count * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
@@ -484,9 +527,17 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
     HG_CUDA(c, cudaMemcpyAsync(c->st.v, vel, 3 * n * sizeof(double), cudaMemcpyDefault, c->stream));
     int32_t flag = 0;
     int rc = device_check(
-        c, [&](int32_t *f) { return launch_validate_init(c->st.mass, c->st.x, c->st.v, n, f, c->stream); }, &flag);
+        c,
+        [&](int32_t *f) {
+            return launch_validate_init(c->st.mass, c->st.x, c->st.v, n, value_limits(c->mixed), f, c->stream);
+        },
+        &flag);
     if (rc) return rc;
-    if (flag) return fail(c, HG_EINVAL, "masses must be finite and > 0, positions and velocities finite");
+    if (flag)
+        return fail(c, HG_EINVAL,
+                    c->mixed ? "masses must be finite and > 0, |positions| <= 1e15 and |velocities| <= 1e30 (the "
+                               "FP32 range of the mixed pair arithmetic)"
+                             : "masses must be finite and > 0, |positions| and |velocities| <= 1e150");
 
     // Start-up: every particle active at t = 0; the prediction is the identity.
     for (double *p : {c->st.a, c->st.j, c->st.s, c->st.c})
@@ -925,21 +976,29 @@ int hg_advance(hg_ctx *c, double t_end, int64_t *steps_out)
         // once): at most one such graph runs per call.
         static_assert(offsetof(DevScalars, err) == offsetof(DevScalars, done) + sizeof(int32_t),
                       "done and err are adjacent");
+        // A failed CUDA call ends the loop with its status (not a return), so
+        // that the stop time is reset and the stream drained below.
+        auto cuda_rc = [&](cudaError_t e, const char *what) {
+            return e == cudaSuccess ? HG_OK : fail(c, HG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+        };
         for (int64_t k = 0;; ++k) {
             const int slot = (int)(k & 1);
             if ((rc = replay(c, true)) != HG_OK) break;
             int32_t *flags = c->h_flags + 2 * slot;
-            HG_CUDA(c, cudaMemcpyAsync(flags, &c->d_sc->done, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                                       c->stream));
-            HG_CUDA(c, cudaEventRecord(c->ev_flags[slot], c->stream));
+            rc = cuda_rc(cudaMemcpyAsync(flags, &c->d_sc->done, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                         c->stream),
+                         "flag copy");
+            if (rc == HG_OK) rc = cuda_rc(cudaEventRecord(c->ev_flags[slot], c->stream), "flag event");
+            if (rc) break;
             if (k == 0) continue;
             const int prev = slot ^ 1;
-            HG_CUDA(c, cudaEventSynchronize(c->ev_flags[prev]));
+            if ((rc = cuda_rc(cudaEventSynchronize(c->ev_flags[prev]), "flag wait")) != HG_OK) break;
             const int32_t *pf = c->h_flags + 2 * prev;
             if (pf[1] & ERR_TIMEOUT) break;   // reported by the final read below
             if (pf[0]) break;
         }
-        if (rc == HG_OK) rc = sync_scalars(c);
+        const int rs = sync_scalars(c);   // waits for the queued replay whatever happened
+        if (rc == HG_OK) rc = rs;
     }
     int rc2 = upload_scalar(c, &c->d_sc->t_stop, INFINITY);
     if (rc) return rc;
@@ -1016,13 +1075,15 @@ int hg_set_state(hg_ctx *c, const hg_state *in)
     int rc = device_check(
         c,
         [&](int32_t *fl) {
-            return launch_validate_state(c->st2, n, c->opts.dt_min, c->opts.dt_max, fl, c->stream);
+            return launch_validate_state(c->st2, n, c->opts.dt_min, c->opts.dt_max, value_limits(c->mixed), fl,
+                                         c->stream);
         },
         &flag);
     if (rc) return rc;
     if (flag)
         return fail(c, HG_EINVAL,
-                    "state check failed: masses > 0, finite values, dt a power of two in [dt_min, dt_max], t a "
+                    "state check failed: masses > 0, finite values within the limits (mixed: |positions| <= "
+                    "1e15, other fields <= 1e30; FP64: 1e150), dt a power of two in [dt_min, dt_max], t a "
                     "multiple of dt");
     // Copy into the live arrays (captured graphs keep their pointers).
     const State &d = c->st, &s = c->st2;
@@ -1084,7 +1145,11 @@ int hg_bind_device(hg_ctx *c, const hg_state *dev, int copy_in)
         } else {
             int32_t flag = 0;
             rc = device_check(
-                c, [&](int32_t *fl) { return launch_validate_state(b, n, c->opts.dt_min, c->opts.dt_max, fl, c->stream); },
+                c,
+                [&](int32_t *fl) {
+                    return launch_validate_state(b, n, c->opts.dt_min, c->opts.dt_max, value_limits(c->mixed), fl,
+                                                 c->stream);
+                },
                 &flag);
             if (rc) return rc;
             if (flag) return fail(c, HG_EINVAL, "the bound arrays do not hold a valid state");
@@ -1140,6 +1205,46 @@ int hg_tune(hg_ctx *c, int64_t m_max, int32_t reps, hg_tune_entry *report, int32
     return rc;
 }
 
+int hg_time_evaluate(hg_ctx *c, const int32_t *idx, int64_t m, int32_t reps, double *us)
+{
+    if (!c || !us) return HG_EINVAL;
+    if (isnan(c->t_pred)) return fail(c, HG_ESTATE, "hg_time_evaluate needs a preceding hg_predict");
+    if (m < 1 || m > c->n || !idx) return fail(c, HG_EINVAL, "m must be in [1, n] and idx given");
+    if (reps < 0 || reps > 1000) return fail(c, HG_EINVAL, "reps must be in [0, 1000]");
+    if (is_device_ptr(idx)) {
+        HG_CUDA(c, cudaMemcpyAsync(c->d_idx2, idx, m * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream));
+        int32_t flag = 0;
+        int rc = device_check(c, [&](int32_t *f) { return launch_validate_idx(c->d_idx2, m, c->n, f, c->stream); },
+                              &flag);
+        if (rc) return rc;
+        if (flag) return fail(c, HG_EINVAL, "idx must be strictly increasing and in [0, n)");
+    } else {
+        for (int64_t q = 0; q < m; ++q)
+            if (idx[q] < 0 || idx[q] >= c->n || (q > 0 && idx[q] <= idx[q - 1]))
+                return fail(c, HG_EINVAL, "idx must be strictly increasing and in [0, n)");
+        HG_CUDA(c, cudaMemcpyAsync(c->d_idx2, idx, m * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    }
+    int32_t *t = c->d_idx;
+    c->d_idx = c->d_idx2;
+    c->d_idx2 = t;
+    drop_graphs(c);   // they captured the old list pointer
+    const double t_pred = c->t_pred;
+    invalidate(c);    // the results buffers are overwritten: no evaluation is pending
+    c->t_pred = t_pred;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    HG_CUDA(c, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(c, HG_ECUDA, "cudaEventCreate failed");
+    }
+    int r = reps;
+    int rc = time_eval(c, m, &r, e0, e1, us);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    return sync_scalars(c);
+}
+
 int hg_get_tuning(hg_ctx *c, int16_t *table)
 {
     if (!c || !table) return HG_EINVAL;
@@ -1157,6 +1262,16 @@ int hg_set_tuning(hg_ctx *c, const int16_t *table)
     }
     for (int k = 0; k < kTuneBuckets; ++k) c->pp.tuned[k] = table[k];
     drop_graphs(c);
+    return HG_OK;
+}
+
+int hg_inject_fault(int32_t kind, int64_t nth)
+{
+    if (kind != HG_FAULT_NONE && kind != HG_FAULT_ALLOC && kind != HG_FAULT_CUDA) return HG_EINVAL;
+    if (kind != HG_FAULT_NONE && nth < 1) return HG_EINVAL;
+    g_fault_kind.store(HG_FAULT_NONE);
+    g_fault_left.store(kind == HG_FAULT_NONE ? 0 : nth);
+    g_fault_kind.store(kind);
     return HG_OK;
 }
 

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "hg.h"
 
@@ -301,6 +302,84 @@ int eval_launches(bool mixed, const EvalArgs &args);
 // 256 threads, a few per SM).
 cudaError_t launch_reduce(const EvalArgs &args, double *ra, double *rj, double *rs, int grid, cudaStream_t st);
 
+// Bit patterns of IEEE-754 values (host and device).
+__host__ __device__ __forceinline__ unsigned long long bits_of(double x)
+{
+#if defined(__CUDA_ARCH__)
+    return (unsigned long long)__double_as_longlong(x);
+#else
+    unsigned long long b;
+    memcpy(&b, &x, sizeof b);
+    return b;
+#endif
+}
+__host__ __device__ __forceinline__ unsigned int bits_of(float x)
+{
+#if defined(__CUDA_ARCH__)
+    return __float_as_uint(x);
+#else
+    unsigned int b;
+    memcpy(&b, &x, sizeof b);
+    return b;
+#endif
+}
+__host__ __device__ __forceinline__ double double_of(unsigned long long b)
+{
+#if defined(__CUDA_ARCH__)
+    return __longlong_as_double((long long)b);
+#else
+    double x;
+    memcpy(&x, &b, sizeof x);
+    return x;
+#endif
+}
+__host__ __device__ __forceinline__ float float_of(unsigned int b)
+{
+#if defined(__CUDA_ARCH__)
+    return __uint_as_float(b);
+#else
+    float x;
+    memcpy(&x, &b, sizeof x);
+    return x;
+#endif
+}
+
+// FP64 <-> FP32 conversions done with integer operations on the IEEE-754
+// encodings (binary64: 1 sign, 11 exponent bits, bias 1023, 52 fraction bits;
+// binary32: 1, 8, bias 127, 23).  GB300's FP64 pipe, which also executes the
+// hardware conversions, is the predictor's limit; the integer pipes are not.
+// d2f: round to nearest, ties to even; results below the smallest normal float
+// (2^-126) become zero of the same sign; magnitudes that round beyond the
+// largest float become infinity of the same sign (IEEE overflow), infinities
+// stay infinities and NaN stays NaN.
+__host__ __device__ __forceinline__ float d2f(double x)
+{
+    const unsigned long long b = bits_of(x);
+    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    const int be = (int)((b >> 52) & 0x7ffu);
+    const int e = be - 1023 + 127;
+    unsigned int m = (unsigned int)((b >> 29) & 0x7fffffu);
+    const unsigned int rem = (unsigned int)b & 0x1fffffffu;
+    m += (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;   // may carry into e
+    const unsigned int mag = ((unsigned int)e << 23) + m;                 // e = 254 carrying gives inf
+    const bool nan = be == 0x7ff && (b & 0xfffffffffffffull) != 0ull;
+    const unsigned int big = nan ? 0x7fc00000u : 0x7f800000u;             // overflow, inf or NaN
+    return float_of(e <= 0 ? sign : (e >= 255 ? (sign | big) : (sign | mag)));
+}
+
+// Exact widening of a float that is zero, normal, infinite or NaN (subnormal
+// floats, which the FP32 arithmetic here flushes, widen to zero).
+__host__ __device__ __forceinline__ double f2d(float f)
+{
+    const unsigned int u = bits_of(f);
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    const unsigned int e = (u >> 23) & 0xffu;
+    const unsigned long long frac = (unsigned long long)(u & 0x7fffffu) << 29;
+    const unsigned long long mag = ((unsigned long long)(e + (1023u - 127u)) << 52) | frac;
+    const unsigned long long special = (0x7ffull << 52) | frac;             // inf (frac 0) or NaN
+    return double_of(e == 0u ? sign : (sign | (e == 255u ? special : mag)));
+}
+
 // ---------------------------------------------------------------------------
 // PTX helpers: mbarrier and bulk (TMA) copies global -> shared.
 // ---------------------------------------------------------------------------
@@ -367,35 +446,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
             smem_addr(dst)),
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
-}
-
-// FP64 <-> FP32 conversions done with integer operations on the IEEE-754
-// encodings (binary64: 1 sign, 11 exponent bits, bias 1023, 52 fraction bits;
-// binary32: 1, 8, bias 127, 23).  GB300's FP64 pipe, which also executes the
-// hardware conversions, is the predictor's limit; the integer pipes are not.
-// d2f: round to nearest, ties to even; results below the smallest normal float
-// (2^-126) become zero of the same sign.  Inputs are finite.
-__device__ __forceinline__ float d2f(double x)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
-    const int e = (int)((b >> 52) & 0x7ffu) - 1023 + 127;
-    unsigned int m = (unsigned int)((b >> 29) & 0x7fffffu);
-    const unsigned int rem = (unsigned int)b & 0x1fffffffu;
-    m += (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;   // may carry into e
-    const unsigned int mag = ((unsigned int)e << 23) + m;
-    return __uint_as_float(e <= 0 ? sign : (sign | mag));
-}
-
-// Exact widening of a float that is zero or normal.
-__device__ __forceinline__ double f2d(float f)
-{
-    const unsigned int u = __float_as_uint(f);
-    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
-    const unsigned int e = (u >> 23) & 0xffu;
-    const unsigned long long mag =
-        ((unsigned long long)(e + (1023u - 127u)) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
-    return __longlong_as_double((long long)(e == 0u ? sign : (sign | mag)));
 }
 
 // Hardware reciprocal square root (single MUFU instruction, flush-to-zero).

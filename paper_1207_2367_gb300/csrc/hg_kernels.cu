@@ -1007,23 +1007,28 @@ __device__ __forceinline__ bool is_pow2(double x)
     return x > 0.0 && isfinite(x) && frexp(x, &e) == 0.5;
 }
 
-__global__ void k_validate_init(const double *mass, const double *x, const double *v, int64_t n, int32_t *flag)
+// |x| <= lim (false for NaN and infinities).
+__device__ __forceinline__ bool within(double x, double lim) { return fabs(x) <= lim; }
+
+__global__ void k_validate_init(const double *mass, const double *x, const double *v, int64_t n, ValueLimits lim,
+                                int32_t *flag)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         bool ok = isfinite(mass[i]) && mass[i] > 0.0;
-        for (int k = 0; k < 3; ++k) ok = ok && isfinite(x[3 * i + k]) && isfinite(v[3 * i + k]);
+        for (int k = 0; k < 3; ++k) ok = ok && within(x[3 * i + k], lim.pos) && within(v[3 * i + k], lim.deriv);
         if (!ok) atomicOr(flag, ERR_VALUE);
     }
 }
 
-__global__ void k_validate_state(const State st, int64_t n, double dt_min, double dt_max, int32_t *flag)
+__global__ void k_validate_state(const State st, int64_t n, double dt_min, double dt_max, ValueLimits lim,
+                                 int32_t *flag)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         bool ok = isfinite(st.mass[i]) && st.mass[i] > 0.0 && isfinite(st.t[i]) && st.t[i] >= 0.0;
         for (int k = 0; k < 3; ++k) {
             const int64_t q = 3 * i + k;
-            ok = ok && isfinite(st.x[q]) && isfinite(st.v[q]) && isfinite(st.a[q]) && isfinite(st.j[q]) &&
-                 isfinite(st.s[q]) && isfinite(st.c[q]);
+            ok = ok && within(st.x[q], lim.pos) && within(st.v[q], lim.deriv) && within(st.a[q], lim.deriv) &&
+                 within(st.j[q], lim.deriv) && within(st.s[q], lim.deriv) && within(st.c[q], lim.deriv);
         }
         const double dt = st.dt[i];
         ok = ok && is_pow2(dt) && dt >= dt_min && dt <= dt_max && fmod(st.t[i], dt) == 0.0;
@@ -1388,17 +1393,17 @@ cudaError_t launch_angular_momentum(const State &st, int64_t n, double t, double
     return cudaGetLastError();
 }
 
-cudaError_t launch_validate_init(const double *mass, const double *x, const double *v, int64_t n, int32_t *flag,
-                                 cudaStream_t s)
+cudaError_t launch_validate_init(const double *mass, const double *x, const double *v, int64_t n,
+                                 const ValueLimits &lim, int32_t *flag, cudaStream_t s)
 {
-    k_validate_init<<<grid_for(n, 256, 4096), 256, 0, s>>>(mass, x, v, n, flag);
+    k_validate_init<<<grid_for(n, 256, 4096), 256, 0, s>>>(mass, x, v, n, lim, flag);
     return cudaGetLastError();
 }
 
-cudaError_t launch_validate_state(const State &st, int64_t n, double dt_min, double dt_max, int32_t *flag,
-                                  cudaStream_t s)
+cudaError_t launch_validate_state(const State &st, int64_t n, double dt_min, double dt_max, const ValueLimits &lim,
+                                  int32_t *flag, cudaStream_t s)
 {
-    k_validate_state<<<grid_for(n, 256, 4096), 256, 0, s>>>(st, n, dt_min, dt_max, flag);
+    k_validate_state<<<grid_for(n, 256, 4096), 256, 0, s>>>(st, n, dt_min, dt_max, lim, flag);
     return cudaGetLastError();
 }
 

@@ -65,10 +65,19 @@ cudaError_t launch_energy(bool mixed, const State &st, int64_t n, double t, doub
 // L = sum_i m_i r_i x v_i of the system predicted to t, into out3 (part3: 3 g doubles).
 cudaError_t launch_angular_momentum(const State &st, int64_t n, double t, double *xe, double *ve, double *part3,
                                     int g, double *out3, cudaStream_t s);
-cudaError_t launch_validate_init(const double *mass, const double *x, const double *v, int64_t n, int32_t *flag,
-                                 cudaStream_t s);
-cudaError_t launch_validate_state(const State &st, int64_t n, double dt_min, double dt_max, int32_t *flag,
-                                  cudaStream_t s);
+// Largest magnitudes a state may hold: pos for positions, deriv for velocities
+// and the higher derivatives (a value beyond them, or not finite, is refused).
+// The mixed path's FP32 pair arithmetic squares position differences and forms
+// products of derivatives and differences, so its limits keep those in FP32's
+// range; the FP64 path's keep them in FP64's.
+struct ValueLimits {
+    double pos, deriv;
+};
+inline ValueLimits value_limits(bool mixed) { return mixed ? ValueLimits{1e15, 1e30} : ValueLimits{1e150, 1e150}; }
+cudaError_t launch_validate_init(const double *mass, const double *x, const double *v, int64_t n,
+                                 const ValueLimits &lim, int32_t *flag, cudaStream_t s);
+cudaError_t launch_validate_state(const State &st, int64_t n, double dt_min, double dt_max, const ValueLimits &lim,
+                                  int32_t *flag, cudaStream_t s);
 cudaError_t launch_validate_idx(const int32_t *idx, int64_t m, int64_t n, int32_t *flag, cudaStream_t s);
 cudaError_t launch_check_correct(const State &st, const int32_t *given, const int32_t *cur, int64_t m, double t_pred,
                                  int32_t *flag, cudaStream_t s);

@@ -84,18 +84,24 @@ __global__ void k_pack(int64_t n, int64_t npad, const double *mass, const double
     }
 }
 
-bool on_device(const void *p)
+// Device (or managed) memory that belongs to device `dev`, the current one: a
+// pointer into another GPU's memory is refused, since the kernels would reach
+// it without peer access.
+bool on_device(const void *p, int dev)
 {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 // Once per device, with that device current: the device address of g_scratch
-// (its host-side name is only a stand-in) and the kernel attributes.
+// (its host-side name is only a stand-in) and the kernel attributes.  Under
+// CUDA's default lazy module loading this is also when the driver loads this
+// file's module on the device and so allocates the array's memory.
 int setup(int dev, Slot **out)
 {
     if (dev < 0 || dev >= kMaxDevices) {
@@ -158,21 +164,21 @@ extern "C" int hg_evaluate_static(int64_t n, const double *mass, const double *p
         set_call_error("every array argument is required");
         return HG_EINVAL;
     }
-    if (m == 0) return HG_OK;
-    const void *ptrs[] = {mass, pos, vel, acc_pred, idx, acc, jerk, snap};
-    for (const void *q : ptrs)
-        if (!on_device(q)) {
-            set_call_error("every array must be device memory");
-            return HG_EINVAL;
-        }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         set_call_error("cudaGetDevice failed");
         return HG_ECUDA;
     }
+    // The first call on a device loads the array (see setup); m = 0 does only that.
     Slot *slot = nullptr;
     int rc = setup(dev, &slot);
-    if (rc) return rc;
+    if (rc || m == 0) return rc;
+    const void *ptrs[] = {mass, pos, vel, acc_pred, idx, acc, jerk, snap};
+    for (const void *q : ptrs)
+        if (!on_device(q, dev)) {
+            set_call_error("every array must be device memory of the current device");
+            return HG_EINVAL;
+        }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool mixed = precision == HG_MIXED;
     unsigned char *base = slot->base;

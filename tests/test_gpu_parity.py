@@ -172,7 +172,8 @@ def test_block_steps_with_injection_match_oracle(hg, precision):
             hg.hg_predict(ctx, tn)
             hg.hg_evaluate(ctx, None, m, acc, jerk, snap)
             ref = sysm.predict_eval(tn, idx_ref)
-            check_eval((acc, jerk, snap), ref, precision, sysm.predict_absum(tn, idx_ref) if precision else None)
+            absum = sysm.predict_absum(tn, idx_ref)
+            check_eval((acc, jerk, snap), ref, precision, absum if precision else None)
             for k, (g, r) in enumerate(zip((acc, jerk, snap), ref)):
                 worst[k] = max(worst[k], np.linalg.norm(g - r) / np.linalg.norm(r))
             hg.hg_correct(ctx, None, m)
@@ -182,6 +183,7 @@ def test_block_steps_with_injection_match_oracle(hg, precision):
             ids = idx_ref
             for f, tol in (("pos", 1e-13 if precision == 0 else 1e-9), ("vel", 1e-12 if precision == 0 else 1e-7)):
                 assert rel_rows(got[f][ids], sysm.get(f)[ids]).max() < tol, f
+            check_corrected_derivatives(got, st, sysm, ids, (acc, jerk, snap), absum, precision)
             np.testing.assert_array_equal(got["t"], sysm.get("t"))
             dt_mismatch += int(np.sum(got["dt"][ids] != sysm.get("dt")[ids]))
             active += m
@@ -189,6 +191,46 @@ def test_block_steps_with_injection_match_oracle(hg, precision):
         assert dt_mismatch <= (0 if precision == 0 else max(1, active // 200)), (dt_mismatch, active)
     finally:
         hg.hg_free(ctx)
+
+
+def _nrm(x):
+    return np.linalg.norm(np.asarray(x).reshape(-1, 3), axis=1)
+
+
+def check_corrected_derivatives(got, st, sysm, ids, evaluated, absum, precision):
+    """After a correction, element by element for the corrected particles ids:
+    - the stored acc, jerk, snap are the evaluated ones (bitwise) and match the
+      oracle's step (the evaluation metric);
+    - the stored crackle equals the oracle's Hermite interpolant (reading R5)
+      applied to the same inputs (old a, jerk, snap from the injected state, the
+      GPU's new ones) within FP64 rounding: 1e-13 of the formula's condition
+      scale S_c = (60 (|a1| + |a0| + |j0| h + |s0| h^2/2) + 36 (|j1| + |j0| +
+      |s0| h) h + 9 (|s1| + |s0|) h^2) / h^3;
+    - the stored crackle matches the oracle's own step within what the
+      evaluation tolerance allows: (60 da + 36 dj h + 9 ds h^2) / h^3 with da,
+      dj, ds the tolerated errors of the new acc, jerk, snap (FP64: 1e-12 of
+      their norms; mixed: 1e-6 / 1e-5 / 1e-4 of the condition scales), plus the
+      rounding term above."""
+    acc, jerk, snap = evaluated
+    for f, g in (("acc", acc), ("jerk", jerk), ("snap", snap)):
+        np.testing.assert_array_equal(got[f][ids], g, err_msg=f)
+    check_eval(tuple(got[f][ids] for f in ("acc", "jerk", "snap")),
+               tuple(sysm.get(f)[ids] for f in ("acc", "jerk", "snap")), precision, absum if precision else None)
+    h = st["dt"][ids]
+    a0, j0, s0 = st["acc"][ids], st["jerk"][ids], st["snap"][ids]
+    c_same = np.stack([oracle.interp(h[q], a0[q], j0[q], s0[q], acc[q], jerk[q], snap[q])[0]
+                       for q in range(len(ids))])
+    Sc = (60.0 * (_nrm(acc) + _nrm(a0) + _nrm(j0) * h + _nrm(s0) * h ** 2 / 2)
+          + 36.0 * (_nrm(jerk) + _nrm(j0) + _nrm(s0) * h) * h + 9.0 * (_nrm(snap) + _nrm(s0)) * h ** 2) / h ** 3
+    dc = _nrm(got["crackle"][ids] - c_same)
+    assert (dc / Sc).max() <= 1e-13, (dc / Sc).max()
+    if precision == 0:
+        da, dj, ds = 1e-12 * _nrm(acc), 1e-12 * _nrm(jerk), 1e-12 * _nrm(snap)
+    else:
+        da, dj, ds = 1e-6 * absum[:, 0], 1e-5 * absum[:, 1], 1e-4 * absum[:, 2]
+    bound = (60.0 * da + 36.0 * dj * h + 9.0 * ds * h ** 2) / h ** 3 + 1e-13 * Sc
+    dref = _nrm(got["crackle"][ids] - sysm.get("crackle")[ids])
+    assert np.all(dref <= bound), (dref / bound).max()
 
 
 # --------------------------------------------------------------------------

@@ -265,3 +265,177 @@ def test_identical_contexts_stay_bitwise_identical(hg, precision):
     finally:
         hg.hg_free(a)
         hg.hg_free(b)
+
+
+def test_time_evaluate_measures_without_changing_state(hg):
+    """hg_time_evaluate times the evaluation of a list and keeps nothing: the
+    state is unchanged, no evaluation is pending, and a following evaluation of
+    the same list still matches the oracle."""
+    n, eps = 3000, 1e-3
+    from gpu_util import gpu_context, gpu_eval, oracle_system
+    sysm = oracle_system(n, 23, eps, steps=2)
+    ctx = gpu_context(hg, sysm, 1, eps)
+    try:
+        before, _ = gpu_state(hg, ctx, n)
+        t = sysm.t_sys + 1.0 / 256
+        idx = np.arange(0, n, 7, dtype=np.int32)
+        hg.hg_predict(ctx, t)
+        us = hg.hg_time_evaluate(ctx, idx, idx.shape[0], 5)
+        assert 0.0 < us < 1e5
+        with pytest.raises(hg.HGError) as e:
+            hg.hg_correct(ctx, None, idx.shape[0])
+        assert e.value.code == hg.HG_ESTATE
+        with pytest.raises(hg.HGError) as e:
+            hg.hg_time_evaluate(ctx, np.array([3, 1], dtype=np.int32), 2)
+        assert e.value.code == hg.HG_EINVAL
+        after, _ = gpu_state(hg, ctx, n)
+        for f in hg.STATE_FIELDS:
+            np.testing.assert_array_equal(before[f], after[f], err_msg=f)
+        got = gpu_eval(hg, ctx, idx, t)
+        ref = sysm.predict_eval(t, idx)
+        for g, r, tol in zip(got, ref, (1e-6, 1e-5, 1e-4)):
+            assert np.linalg.norm(g - r) / np.linalg.norm(r) <= tol
+    finally:
+        hg.hg_free(ctx)
+
+
+def test_peak_flops_microbenchmark(hg):
+    """The FMA-rate microbenchmark returns rates of the right order for this GPU:
+    FP32 (scalar and packed) near SMs x 128 lanes x 2 flops x clock, FP64 near
+    SMs x 2 DFMA x 2 flops x clock, and never above the nominal figure at the
+    maximum clock by more than a measurement's noise."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    f32_nom = sms * 128 * 2 * 2.2e9 / 1e12      # a little above the 2.07 GHz maximum
+    f64_nom = sms * 2 * 2 * 2.2e9 / 1e12
+    for form, nom in (("f32", f32_nom), ("f32x2", f32_nom), ("f64", f64_nom)):
+        tf, ms = hg.hg_peak_flops(form, 0)
+        assert 0.3 * nom < tf < 1.05 * nom, (form, tf, nom)
+        assert ms > 0.0
+    with pytest.raises(hg.HGError):
+        hg.hg_peak_flops("f32", 999)
+
+
+def test_mixed_context_refuses_values_outside_fp32_range(hg):
+    """The mixed path's FP32 pair arithmetic squares position differences, so a
+    mixed context refuses |positions| > 1e15 and other fields > 1e30 (HG_EINVAL,
+    state unchanged); an FP64 context takes the same positions."""
+    n = 64
+    p = inputs.plummer(n, 30)
+    far = p.pos.copy()
+    far[5, 1] = 1e16
+    with pytest.raises(hg.HGError) as e:
+        hg.hg_init(p.mass, far, p.vel, 1e-3, 0.45, hg.hg_default_opts(precision=hg.HG_MIXED, dt_max=DT_MAX))
+    assert e.value.code == hg.HG_EINVAL and "1e15" in str(e.value)
+    hg.hg_free(hg.hg_init(p.mass, far, p.vel, 1e-3, 0.45, hg.hg_default_opts(precision=hg.HG_FP64, dt_max=DT_MAX)))
+    ctx = hg.hg_init(p.mass, p.pos, p.vel, 1e-3, 0.45, hg.hg_default_opts(precision=hg.HG_MIXED, dt_max=DT_MAX))
+    try:
+        before, t0 = gpu_state(hg, ctx, n)
+        bad = {f: before[f].copy() for f in hg.STATE_FIELDS}
+        bad["crackle"][3, 0] = 1e31
+        with pytest.raises(hg.HGError) as e:
+            hg.hg_set_state(ctx, bad, t0)
+        assert e.value.code == hg.HG_EINVAL
+        after, _ = gpu_state(hg, ctx, n)
+        for f in hg.STATE_FIELDS:
+            np.testing.assert_array_equal(before[f], after[f], err_msg=f)
+    finally:
+        hg.hg_free(ctx)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_section_profile_changes_nothing_and_accounts_for_the_time(hg, precision):
+    """opts.profile = 1 (CUDA events around the sections of every graph-replayed
+    block step, Table 1 sections) leaves the integration bitwise unchanged, counts
+    every block step, and its section times add up to the device time of the
+    replays (CUDA events on the context's stream around the same calls), less the
+    short idle gaps between replays that the host's per-replay wait leaves."""
+    import torch
+    n, eps, steps = 32768, 1e-4, 24
+    p = inputs.plummer(n, 31)
+    stream = torch.cuda.Stream()
+    ctxs = [hg.hg_init(p.mass, p.pos, p.vel, eps, 0.45,
+                       hg.hg_default_opts(precision=precision, dt_max=DT_MAX, profile=prof, stream=stream))
+            for prof in (0, 1)]
+    try:
+        hg.hg_step(ctxs[0], steps)
+        hg.hg_get_profile(ctxs[1], reset=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hg.hg_step(ctxs[1], steps)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms = e0.elapsed_time(e1)
+        prof = hg.hg_get_profile(ctxs[1])
+        assert prof["block_steps"] == steps
+        ms = prof["ms"]
+        assert all(v >= 0.0 for v in ms.values())
+        assert ms["predict"] > 0 and ms["evaluate"] > 0 and ms["correct"] > 0
+        sections = sum(ms.values())
+        assert 0.8 * total_ms <= sections <= 1.001 * total_ms, (sections, total_ms)
+        sa, ta = gpu_state(hg, ctxs[0], n)
+        sb, tb = gpu_state(hg, ctxs[1], n)
+        assert ta == tb
+        for f in hg.STATE_FIELDS:
+            np.testing.assert_array_equal(sa[f], sb[f], err_msg=f)
+        assert hg.hg_get_profile(ctxs[0])["block_steps"] == 0      # unprofiled: nothing recorded
+    finally:
+        for c in ctxs:
+            hg.hg_free(c)
+
+
+def test_injected_allocation_failure_returns_enomem_and_frees_everything(hg):
+    """A device allocation that fails in the middle of hg_init (host-side
+    injection, no device fault) gives HG_ENOMEM, no context, and every
+    allocation made before it is released."""
+    import torch
+    p = inputs.plummer(4096, 32)
+    o = hg.hg_default_opts(precision=hg.HG_MIXED, dt_max=DT_MAX)
+    hg.hg_free(hg.hg_init(p.mass, p.pos, p.vel, 1e-3, 0.45, o))    # module loads and library set-up done
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for nth in (1, 7, 20):
+        hg.hg_inject_fault(hg.HG_FAULT_ALLOC, nth)
+        with pytest.raises(hg.HGError) as e:
+            hg.hg_init(p.mass, p.pos, p.vel, 1e-3, 0.45, o)
+        assert e.value.code == hg.HG_ENOMEM
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0, nth
+    hg.hg_free(hg.hg_init(p.mass, p.pos, p.vel, 1e-3, 0.45, o))    # the injector disarmed itself
+
+
+def test_injected_cuda_failure_returns_ecuda_and_keeps_the_state(hg):
+    """A CUDA call that fails (host-side injection: the call is not made) makes
+    hg_set_state, hg_evaluate and hg_step return HG_ECUDA; a failure before the
+    state is touched leaves it as it was, and the context can still be freed."""
+    from gpu_util import gpu_context, oracle_system
+    n, eps = 512, 1e-3
+    sysm = oracle_system(n, 33, eps, steps=2)
+    ctx = gpu_context(hg, sysm, 1, eps)
+    try:
+        before, t0 = gpu_state(hg, ctx, n)
+        other = {f: before[f].copy() for f in hg.STATE_FIELDS}
+        other["pos"] *= 1.5
+        hg.hg_inject_fault(hg.HG_FAULT_CUDA, 1)          # the first copy into the staging state
+        with pytest.raises(hg.HGError) as e:
+            hg.hg_set_state(ctx, other, t0)
+        assert e.value.code == hg.HG_ECUDA and "injected" in str(e.value)
+        after, t1 = gpu_state(hg, ctx, n)
+        assert t1 == t0
+        for f in hg.STATE_FIELDS:
+            np.testing.assert_array_equal(before[f], after[f], err_msg=f)
+        hg.hg_predict(ctx, t0 + 1.0 / 256)
+        hg.hg_inject_fault(hg.HG_FAULT_CUDA, 2)
+        with pytest.raises(hg.HGError) as e:
+            hg.hg_evaluate(ctx, np.arange(0, n, 3, dtype=np.int32), len(range(0, n, 3)))
+        assert e.value.code == hg.HG_ECUDA
+        hg.hg_inject_fault(hg.HG_FAULT_CUDA, 3)
+        with pytest.raises(hg.HGError) as e:
+            hg.hg_step(ctx, 4)
+        assert e.value.code == hg.HG_ECUDA
+    finally:
+        hg.hg_inject_fault(hg.HG_FAULT_NONE)
+        hg.hg_free(ctx)
+    with pytest.raises(hg.HGError):
+        hg.hg_inject_fault(hg.HG_FAULT_ALLOC, 0)

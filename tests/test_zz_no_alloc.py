@@ -61,6 +61,54 @@ def test_static_entry_matches_context_entry_twice(hg, precision):
         _compare([o.cpu().numpy() for o in out], ref, precision)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_static_entry_at_its_limits(hg, precision):
+    """The largest system the fixed array holds (n = 16384: the full record area)
+    with one active particle (the largest j-split, b * m at its cap), 16, and all
+    of them (m = n); and eps = 0 (the guarded path that skips the own pair)."""
+    import torch
+    n = 16384
+    for eps, lists in ((1e-3, (np.array([n // 2]), np.arange(5, n, n // 16)[:16], np.arange(n))),
+                       (0.0, (np.arange(0, n, 5),))):
+        ctx, st = _system(hg, n, 40, precision, eps)
+        dev = {k: torch.tensor(st[k], device="cuda") for k in ("mass", "pos", "vel", "acc")}
+        try:
+            for idx in lists:
+                idx = np.ascontiguousarray(idx, dtype=np.int32)
+                m = idx.shape[0]
+                ref = [np.empty((m, 3)) for _ in range(3)]
+                hg.hg_evaluate(ctx, idx, m, *ref)
+                out = [torch.full((m, 3), float("nan"), dtype=torch.float64, device="cuda") for _ in range(3)]
+                hg.hg_evaluate_static(dev["mass"], dev["pos"], dev["vel"], dev["acc"], eps, precision,
+                                      torch.tensor(idx, device="cuda"), m, *out)
+                _compare([o.cpu().numpy() for o in out], ref, precision)
+        finally:
+            hg.hg_free(ctx)
+
+
+def test_static_entry_allocates_nothing_after_set_up(hg):
+    """A call with m = 0 loads the fixed array; after one full call, a second
+    call leaves the device's free memory exactly as it was (cudaMemGetInfo)."""
+    import torch
+    n, m, eps = 4096, 1024, 1e-3
+    ctx, st = _system(hg, n, 41, 1, eps)
+    hg.hg_free(ctx)
+    dev = {k: torch.tensor(st[k], device="cuda") for k in ("mass", "pos", "vel", "acc")}
+    idx = torch.arange(0, n, n // m, dtype=torch.int32, device="cuda")
+    out = [torch.empty((m, 3), dtype=torch.float64, device="cuda") for _ in range(3)]
+    args = (dev["mass"], dev["pos"], dev["vel"], dev["acc"], eps, 1, idx)
+    hg.hg_evaluate_static(*args, 0, *out)        # set-up only
+    hg.hg_evaluate_static(*args, m, *out)
+    first = [o.clone() for o in out]
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    hg.hg_evaluate_static(*args, m, *out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    for a, b in zip(first, out):
+        assert torch.equal(a, b)
+
+
 def test_static_entry_rejects_what_it_cannot_hold(hg):
     import torch
     n = 16385
