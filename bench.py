@@ -394,22 +394,29 @@ def run_headline(a, rank, world, dist):
         barrier()
         torch.cuda.synchronize()
         clocks.start()
-        ms, per_step = 0.0, []
+        ms, per_step, m_step, eval_step = 0.0, [], [], []
+        prof = {"ms": {k: 0.0 for k in hg.SECTIONS}, "block_steps": 0}
         torch.cuda.nvtx.range_push("timed")      # ncu --nvtx --nvtx-include "timed/" profiles only these launches
         for _ in range(a.steps):
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            q0 = hg.hg_get_stats(ctx)["interactions"]
             ev0.record(stream)
             hg.hg_step(ctx, bs)
             ev1.record(stream)
             ev1.synchronize()
             per_step.append(ev0.elapsed_time(ev1))
             ms += per_step[-1]
+            m_step.append((hg.hg_get_stats(ctx)["interactions"] - q0) // a.n)   # outside the event pair
+            pr = hg.hg_get_profile(ctx, reset=True)
+            eval_step.append(pr["ms"]["evaluate"])
+            for k, v in pr["ms"].items():
+                prof["ms"][k] += v
+            prof["block_steps"] += pr["block_steps"]
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         clk = clocks.stop()
         barrier()
         s1 = hg.hg_get_stats(ctx)
-        prof = hg.hg_get_profile(ctx)
         inter = s1["interactions"] - s0["interactions"]
         launches = s1["kernels"] - s0["kernels"]
         steps_taken = s1["block_steps"] - s0["block_steps"]
@@ -447,6 +454,8 @@ def run_headline(a, rank, world, dist):
         "interactions": inter,
         "mean_block_size": inter / max(1, steps_taken) / a.n,
         "ms_per_step_each": per_step,
+        "pairs_per_step_over_n": m_step,
+        "eval_ms_per_step": eval_step,
         "startup": {"seconds": startup_s, "interactions": a.n * a.n,
                     "rate": a.n * a.n / startup_s,
                     "note": "hg_init wall time: upload, validation, evaluation with all N active, first steps"},
@@ -505,6 +514,7 @@ def subset_vs_fp64(hg, ctx, p, a, stream, device):
         hg.hg_predict(ctx, t)
         us_mixed = hg.hg_time_evaluate(ctx, lst_d, SUBSET, 3)
         hg.hg_evaluate(ctx, lst, SUBSET, *got)
+        scale = hg.hg_condition_scale(ctx, SUBSET)
         hg.hg_predict(ref, t)
         us_f64 = hg.hg_time_evaluate(ref, lst_d, SUBSET, 1)
         hg.hg_evaluate(ref, lst, SUBSET, *want)
@@ -515,6 +525,7 @@ def subset_vs_fp64(hg, ctx, p, a, stream, device):
                       f"time t = {t_sys!r}",
             "errors_vs_fp64_kernel": {name: _rel_stats(g, w) for name, g, w in
                                       zip(("acc", "jerk", "snap"), got, want)},
+            "acc_conditioning": _kappa_stats(got[0], want[0], scale),
             "tolerance_normwise": {"acc": 1e-6, "jerk": 1e-5, "snap": 1e-4},
             "mixed_rate": pairs / (us_mixed * 1e-6), "fp64_rate": pairs / (us_f64 * 1e-6),
             "mixed_over_fp64": us_f64 / us_mixed, "unit": "interactions/s (evaluation + reduction kernels)"}
@@ -823,6 +834,22 @@ def _device_state(hg, ctx, n):
     return st, t
 
 
+def _kappa_stats(got_acc, ref_acc, scale):
+    """Acceleration errors against the condition scale sum_j m_j / (r_ij^2 + eps^2)
+    (hg_condition_scale): the worst per-particle relative error with that
+    particle's condition number kappa = scale / |a|, the largest error relative
+    to the scale, and the median kappa."""
+    g, r = np.asarray(got_acc).reshape(-1, 3), np.asarray(ref_acc).reshape(-1, 3)
+    err = np.linalg.norm(g - r, axis=1)
+    rn = np.linalg.norm(r, axis=1)
+    per = err / np.where(rn > 0, rn, 1.0)
+    kappa = scale / np.where(rn > 0, rn, 1.0)
+    w = int(np.argmax(per))
+    return {"worst_particle_rel_err": float(per[w]), "worst_particle_kappa": float(kappa[w]),
+            "max_err_over_scale": float((err / scale).max()), "median_kappa": float(np.median(kappa)),
+            "max_kappa": float(kappa.max())}
+
+
 def _rel_stats(got, ref):
     """Normwise and per-particle relative errors of an [m][3] result."""
     g, r = np.asarray(got).reshape(-1, 3), np.asarray(ref).reshape(-1, 3)
@@ -1002,6 +1029,7 @@ def run_accuracy(a):
         want = [np.empty((m, 3)) for _ in range(3)]
         hg.hg_predict(mix, t)
         hg.hg_evaluate(mix, None, m, *got)
+        scale = hg.hg_condition_scale(mix, m)
         hg.hg_predict(ref, t)
         hg.hg_evaluate(ref, lst, m, *want)
         hg.hg_correct(mix, None, m)
@@ -1009,6 +1037,7 @@ def run_accuracy(a):
         for name, g, w in zip(("acc", "jerk", "snap"), got, want):
             row[name] = _rel_stats(g, w)
             worst[name] = max(worst[name], row[name]["normwise"])
+        row["acc_conditioning"] = _kappa_stats(got[0], want[0], scale)
         per_step.append(row)
         del st
     hg.hg_free(ref)
@@ -1030,6 +1059,9 @@ def run_accuracy(a):
         "tolerance": {"acc": 1e-6, "jerk": 1e-5, "snap": 1e-4},
         "max_normwise": worst,
         "max_per_particle": {k: max(r[k]["max"] for r in per_step) for k in ("acc", "jerk", "snap")},
+        "acc_worst_particle": max((r["acc_conditioning"] for r in per_step),
+                                  key=lambda c: c["worst_particle_rel_err"]),
+        "acc_max_err_over_scale": max(r["acc_conditioning"]["max_err_over_scale"] for r in per_step),
         "median_per_particle": {k: float(np.median([r[k]["median"] for r in per_step]))
                                 for k in ("acc", "jerk", "snap")},
         "block_sizes": {"min": min(ms), "max": max(ms), "mean": float(np.mean(ms))},

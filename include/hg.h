@@ -148,6 +148,18 @@ int hg_predict(hg_ctx *ctx, double t);
  * HG_ESTATE (no prediction), HG_ECUDA, HG_ETIMEOUT. */
 int hg_evaluate(hg_ctx *ctx, const int32_t *idx, int64_t m, double *acc, double *jerk, double *snap);
 
+/* The condition scale of the last hg_evaluate of a mixed context: for each of
+ * its m particles (in the order of its list), sum_{j != i} m_j / (r_ij^2 +
+ * eps^2) over the predicted data, summed in FP32 like the evaluation (an upper
+ * bound of sum_j |a_ij|, equal to it for r_ij >> eps).  FP32 rounding of the
+ * pair terms errs in a_i in proportion to it, so scale_i / |a_i| is the
+ * particle's condition number; the step criterion's noise floor uses it too.
+ * out: [m] doubles, host or device.  Errors: HG_ESTATE (FP64 context, or no
+ * pending evaluation), HG_EINVAL (m differs from the evaluation's).
+ * Synchronizes.  (The paper has no counterpart: its hybrid precision has no
+ * noise analysis.) */
+int hg_condition_scale(hg_ctx *ctx, double *out, int64_t m);
+
 /* Sect. 3 item 3 and the time-step update: correct the particles of the last
  * hg_evaluate (idx NULL, or the same list), derive crackle from the Hermite
  * interpolant, take the new step from the p = 6 criterion quantized to powers

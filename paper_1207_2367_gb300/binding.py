@@ -107,13 +107,14 @@ def load(path: str | None = None):
         L.hg_bind_device.argtypes = [P, C.c_void_p, C.c_int]
         L.hg_tune.argtypes = [P, I64, C.c_int32, C.POINTER(hg_tune_entry), C.c_int32, C.POINTER(C.c_int32)]
         L.hg_time_evaluate.argtypes = [P, I32P, I64, C.c_int32, C.POINTER(D)]
+        L.hg_condition_scale.argtypes = [P, P, I64]
         L.hg_inject_fault.argtypes = [C.c_int32, I64]
         L.hg_inject_fault.restype = C.c_int
         L.hg_get_tuning.argtypes = [P, C.POINTER(C.c_int16)]
         L.hg_set_tuning.argtypes = [P, C.POINTER(C.c_int16)]
         for name in ("hg_init", "hg_next_block", "hg_predict", "hg_evaluate", "hg_correct", "hg_step",
                      "hg_advance", "hg_energy", "hg_get_state", "hg_set_state", "hg_get_stats", "hg_get_profile",
-                     "hg_tune", "hg_time_evaluate", "hg_get_tuning", "hg_set_tuning", "hg_angular_momentum", "hg_bind_device"):
+                     "hg_tune", "hg_time_evaluate", "hg_condition_scale", "hg_get_tuning", "hg_set_tuning", "hg_angular_momentum", "hg_bind_device"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -194,6 +195,13 @@ def hg_predict(ctx, t):
 
 def hg_evaluate(ctx, idx, m, acc=None, jerk=None, snap=None):
     _check(ctx, load().hg_evaluate(ctx, _ptr(idx, np.int32), int(m), _ptr(acc), _ptr(jerk), _ptr(snap)))
+
+
+def hg_condition_scale(ctx, m, out=None):
+    """sum_j m_j / (r_ij^2 + eps^2) of the last mixed evaluation's m particles."""
+    out = np.empty(int(m)) if out is None else out
+    _check(ctx, load().hg_condition_scale(ctx, _ptr(out), int(m)))
+    return out
 
 
 def hg_correct(ctx, idx, m):

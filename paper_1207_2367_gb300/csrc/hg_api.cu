@@ -897,6 +897,16 @@ int hg_evaluate(hg_ctx *c, const int32_t *idx, int64_t m, double *acc, double *j
     return HG_OK;
 }
 
+int hg_condition_scale(hg_ctx *c, double *out, int64_t m)
+{
+    if (!c) return HG_EINVAL;
+    if (!c->mixed) return fail(c, HG_ESTATE, "the FP64 evaluation does not form the condition scale");
+    if (c->eval_m < 0) return fail(c, HG_ESTATE, "hg_condition_scale needs a preceding hg_evaluate");
+    if (m != c->eval_m || (m > 0 && !out)) return fail(c, HG_EINVAL, "m differs from the last hg_evaluate");
+    if (m > 0) HG_CUDA(c, cudaMemcpyAsync(out, c->rn, m * sizeof(double), cudaMemcpyDefault, c->stream));
+    return sync_scalars(c);
+}
+
 int hg_correct(hg_ctx *c, const int32_t *idx, int64_t m)
 {
     if (!c) return HG_EINVAL;

@@ -45,3 +45,14 @@ def test_clock_samples_and_throttle_reasons():
     hot = bench.parse_clock_samples(["0, 1500, 2070, 1400, 0x48, Active, Active, Not Active, Not Active\n"])
     assert hot["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
     assert bench.parse_clock_samples([])["reasons"] == ["no samples"]
+
+
+def test_kappa_statistics():
+    import numpy as np
+    ref = np.array([[1.0, 0.0, 0.0], [0.0, 1e-3, 0.0]])
+    got = ref + np.array([[1e-7, 0.0, 0.0], [0.0, 1e-8, 0.0]])
+    scale = np.array([2.0, 1.0])
+    st = bench._kappa_stats(got, ref, scale)
+    assert abs(st["worst_particle_rel_err"] - 1e-5) < 1e-15        # particle 2: 1e-8 / 1e-3
+    assert abs(st["worst_particle_kappa"] - 1e3) < 1e-9             # 1.0 / 1e-3
+    assert abs(st["max_err_over_scale"] - 5e-8) < 1e-15            # particle 1: 1e-7 / 2

@@ -488,3 +488,40 @@ def test_device_pointers_and_torch_stream(hg):
         check_eval([o.cpu().numpy() for o in out], ref, 1, sysm.predict_absum(t, idx.cpu().numpy()))
     finally:
         hg.hg_free(ctx)
+
+
+def test_condition_scale_of_the_mixed_evaluation(hg):
+    """hg_condition_scale returns, per evaluated particle, sum_{j != i} m_j /
+    (r_ij^2 + eps^2) over the predicted data (the definition, summed here in
+    numpy from the oracle's prediction), which bounds the oracle's sum_j |a_ij|
+    from above; FP64 contexts do not form it."""
+    n, eps = 3001, 1e-3
+    sysm = oracle_system(n, 24, eps, steps=2)
+    t = sysm.t_sys + 1.0 / 512
+    idx = np.arange(5, n, 11)
+    st = sysm.get_state()
+    xp, _, _ = oracle.predict(st["pos"], st["vel"], st["acc"], st["jerk"], st["snap"], st["crackle"], st["t"], t)
+    ctx = gpu_context(hg, sysm, 1, eps)
+    try:
+        gpu_eval(hg, ctx, idx, t)
+        sc = hg.hg_condition_scale(ctx, len(idx))
+        with pytest.raises(hg.HGError) as e:
+            hg.hg_condition_scale(ctx, len(idx) - 1)
+        assert e.value.code == hg.HG_EINVAL
+    finally:
+        hg.hg_free(ctx)
+    for q, i in enumerate(idx):
+        d2 = np.sum((xp - xp[i]) ** 2, axis=1) + eps * eps
+        mask = np.arange(n) != i
+        ref = np.sum(st["mass"][mask] / d2[mask])
+        assert abs(sc[q] - ref) <= 1e-5 * ref, (q, sc[q], ref)
+    absum = sysm.predict_absum(t, idx)[:, 0]
+    assert np.all(sc >= absum * (1 - 1e-5))
+    ctx = gpu_context(hg, sysm, 0, eps)
+    try:
+        gpu_eval(hg, ctx, idx, t)
+        with pytest.raises(hg.HGError) as e:
+            hg.hg_condition_scale(ctx, len(idx))
+        assert e.value.code == hg.HG_ESTATE
+    finally:
+        hg.hg_free(ctx)
