@@ -354,6 +354,19 @@ int hg_set_tuning(hg_ctx *ctx, const int16_t *table);
 #define HG_FAULT_CUDA 2
 int hg_inject_fault(int32_t kind, int64_t nth);
 
+/* The checked build (compiled with -DHG_CHECKED, paper_1207_2367_gb300/_lib/
+ * libhgpu_checked.so) adds device bounds checks on every active-list entry,
+ * j-tile range and partial-sum row the evaluation, reduction and correction
+ * kernels touch: a value out of range is not used (the access is skipped or
+ * clamped) and the next synchronizing call returns HG_ECUDA with a message,
+ * instead of a memory fault.  hg_build_checked() returns 1 in that build, 0 in
+ * the normal one.  Testing only: hg_test_corrupt_list writes value into entry
+ * pos of the context's current block list (after hg_next_block), so that the
+ * checks can be seen to fire; the normal build refuses it (HG_EINVAL) and
+ * touches nothing.  (Library conveniences; the paper has no counterpart.) */
+int hg_build_checked(void);
+int hg_test_corrupt_list(hg_ctx *ctx, int64_t pos, int32_t value);
+
 /* Release the context and its device memory.  NULL is allowed. */
 void hg_free(hg_ctx *ctx);
 

@@ -67,12 +67,14 @@ _lock = threading.Lock()
 
 
 def load(path: str | None = None):
-    """Build (if needed) and load the CUDA library; raises on failure."""
+    """Build (if needed) and load the CUDA library; raises on failure.  The
+    environment variable HG_LIB_VARIANT=checked selects the checked build
+    (device bounds checks that report instead of faulting)."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        path = path or _build.build()
+        path = path or _build.build(checked=os.environ.get("HG_LIB_VARIANT", "") == "checked")
         L = C.CDLL(path)
         P, I64, D, I32P = C.c_void_p, C.c_int64, C.c_double, C.c_void_p
         L.hg_default_opts.argtypes = [C.POINTER(hg_opts)]
@@ -108,6 +110,10 @@ def load(path: str | None = None):
         L.hg_tune.argtypes = [P, I64, C.c_int32, C.POINTER(hg_tune_entry), C.c_int32, C.POINTER(C.c_int32)]
         L.hg_time_evaluate.argtypes = [P, I32P, I64, C.c_int32, C.POINTER(D)]
         L.hg_condition_scale.argtypes = [P, P, I64]
+        L.hg_build_checked.argtypes = []
+        L.hg_build_checked.restype = C.c_int
+        L.hg_test_corrupt_list.argtypes = [P, I64, C.c_int32]
+        L.hg_test_corrupt_list.restype = C.c_int
         L.hg_inject_fault.argtypes = [C.c_int32, I64]
         L.hg_inject_fault.restype = C.c_int
         L.hg_get_tuning.argtypes = [P, C.POINTER(C.c_int16)]
@@ -329,6 +335,16 @@ def hg_inject_fault(kind, nth=0):
     rc = load().hg_inject_fault(int(kind), int(nth))
     if rc != HG_OK:
         raise HGError(rc, "bad fault kind or count")
+
+
+def hg_build_checked():
+    """True when the loaded library is the checked build."""
+    return bool(load().hg_build_checked())
+
+
+def hg_test_corrupt_list(ctx, pos, value):
+    """Testing (checked build only): write value into entry pos of the current block list."""
+    _check(ctx, load().hg_test_corrupt_list(ctx, int(pos), int(value)))
 
 
 def hg_size(ctx):

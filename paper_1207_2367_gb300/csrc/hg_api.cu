@@ -3,6 +3,7 @@
 // stepping loop.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
 #include <stdint.h>
 #include <string.h>
@@ -66,6 +67,15 @@ struct hg_ctx {
 namespace {
 
 thread_local std::string g_init_err;
+
+// NVTX range named after the C ABI call for the duration of the call (a no-op
+// unless a profiler is attached), e.g. ncu --nvtx --nvtx-include "hg_step/".
+struct CallRange {
+    explicit CallRange(const char *name) { nvtxRangePushA(name); }
+    ~CallRange() { nvtxRangePop(); }
+    CallRange(const CallRange &) = delete;
+    CallRange &operator=(const CallRange &) = delete;
+};
 
 int fail(hg_ctx *c, int code, const std::string &msg)
 {
@@ -186,6 +196,8 @@ EvalArgs eval_args(hg_ctx *c, const int64_t *m_dev, int64_t m_host)
     EvalArgs a;
     a.rec = c->rec;
     a.npad = c->npad;
+    a.n = c->n;
+    a.pcap = c->pcap;
     a.idx = c->d_idx;
     a.m_dev = m_dev;
     a.m_host = m_host;
@@ -232,6 +244,9 @@ int sync_scalars(hg_ctx *c)
     HG_CUDA(c, cudaMemcpyAsync(c->h_sc, c->d_sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
     HG_CUDA(c, cudaStreamSynchronize(c->stream));
     if (c->h_sc->err & ERR_TIMEOUT) return fail(c, HG_ETIMEOUT, "a bounded device wait expired");
+    if (c->h_sc->err & ERR_BOUNDS)
+        return fail(c, HG_ECUDA, "a device bounds check failed (checked build): an index, tile or partial-sum row "
+                                 "was out of range and its access skipped");
     return HG_OK;
 }
 
@@ -757,6 +772,7 @@ int hg_init(hg_ctx **out, int64_t n, const double *mass, const double *pos, cons
 int hg_init_batch(hg_ctx **out, int32_t n_clusters, const int64_t *offsets, int64_t n, const double *mass,
                   const double *pos, const double *vel, double eps, double eta, const hg_opts *opts)
 {
+    const CallRange range_("hg_init_batch");
     g_init_err.clear();
     auto bad = [](const char *m) {
         g_init_err = m;
@@ -824,6 +840,7 @@ int hg_init_batch(hg_ctx **out, int32_t n_clusters, const int64_t *offsets, int6
 
 int hg_next_block(hg_ctx *c, double *t_next, int32_t *idx, int64_t cap, int64_t *m_out)
 {
+    const CallRange range_("hg_next_block");
     if (!c) return HG_EINVAL;
     HG_CUDA(c, launch_next_block(c->st, c->n, c->nb_part, c->nb_cnt, c->nb_off, c->d_idx, c->d_sc, 0, c->pp,
                                  c->stream));
@@ -845,6 +862,7 @@ int hg_next_block(hg_ctx *c, double *t_next, int32_t *idx, int64_t cap, int64_t 
 
 int hg_predict(hg_ctx *c, double t)
 {
+    const CallRange range_("hg_predict");
     if (!c) return HG_EINVAL;
     if (!isfinite(t)) return fail(c, HG_EINVAL, "t must be finite");
     HG_CUDA(c, launch_predict(c->mixed, c->st, c->rec, c->n, c->npad, nullptr, t, nullptr, rmap_of(c), c->stream));
@@ -856,6 +874,7 @@ int hg_predict(hg_ctx *c, double t)
 
 int hg_evaluate(hg_ctx *c, const int32_t *idx, int64_t m, double *acc, double *jerk, double *snap)
 {
+    const CallRange range_("hg_evaluate");
     if (!c) return HG_EINVAL;
     if (isnan(c->t_pred)) return fail(c, HG_ESTATE, "hg_evaluate needs a preceding hg_predict");
     if (m < 0 || m > c->n) return fail(c, HG_EINVAL, "m must be in [0, n]");
@@ -899,6 +918,7 @@ int hg_evaluate(hg_ctx *c, const int32_t *idx, int64_t m, double *acc, double *j
 
 int hg_condition_scale(hg_ctx *c, double *out, int64_t m)
 {
+    const CallRange range_("hg_condition_scale");
     if (!c) return HG_EINVAL;
     if (!c->mixed) return fail(c, HG_ESTATE, "the FP64 evaluation does not form the condition scale");
     if (c->eval_m < 0) return fail(c, HG_ESTATE, "hg_condition_scale needs a preceding hg_evaluate");
@@ -909,6 +929,7 @@ int hg_condition_scale(hg_ctx *c, double *out, int64_t m)
 
 int hg_correct(hg_ctx *c, const int32_t *idx, int64_t m)
 {
+    const CallRange range_("hg_correct");
     if (!c) return HG_EINVAL;
     if (c->eval_m < 0) return fail(c, HG_ESTATE, "hg_correct needs a preceding hg_evaluate");
     if (m != c->eval_m) return fail(c, HG_EINVAL, "m differs from the last hg_evaluate");
@@ -923,7 +944,7 @@ int hg_correct(hg_ctx *c, const int32_t *idx, int64_t m)
     }
     int32_t flag = 0;
     int rc = device_check(
-        c, [&](int32_t *f) { return launch_check_correct(c->st, given, c->d_idx, m, c->eval_t, f, c->stream); },
+        c, [&](int32_t *f) { return launch_check_correct(c->st, given, c->d_idx, m, c->n, c->eval_t, f, c->stream); },
         &flag);
     if (rc) return rc;
     if (flag)
@@ -942,6 +963,7 @@ int hg_correct(hg_ctx *c, const int32_t *idx, int64_t m)
 
 int hg_step(hg_ctx *c, int64_t n_steps)
 {
+    const CallRange range_("hg_step");
     if (!c) return HG_EINVAL;
     if (n_steps < 0) return fail(c, HG_EINVAL, "n_steps must be >= 0");
     if (n_steps == 0) return HG_OK;
@@ -959,6 +981,7 @@ int hg_step(hg_ctx *c, int64_t n_steps)
 
 int hg_advance(hg_ctx *c, double t_end, int64_t *steps_out)
 {
+    const CallRange range_("hg_advance");
     if (!c) return HG_EINVAL;
     if (!isfinite(t_end)) return fail(c, HG_EINVAL, "t_end must be finite");
     int rc = ensure_graphs(c);
@@ -1019,6 +1042,7 @@ int hg_advance(hg_ctx *c, double t_end, int64_t *steps_out)
 
 int hg_energy(hg_ctx *c, double *kinetic, double *potential)
 {
+    const CallRange range_("hg_energy");
     if (!c) return HG_EINVAL;
     int rc = sync_scalars(c);
     if (rc) return rc;
@@ -1035,6 +1059,7 @@ int hg_energy(hg_ctx *c, double *kinetic, double *potential)
 
 int hg_angular_momentum(hg_ctx *c, double *L)
 {
+    const CallRange range_("hg_angular_momentum");
     if (!c || !L) return HG_EINVAL;
     int rc = sync_scalars(c);
     if (rc) return rc;
@@ -1049,6 +1074,7 @@ int hg_angular_momentum(hg_ctx *c, double *L)
 
 int hg_get_state(hg_ctx *c, hg_state *o)
 {
+    const CallRange range_("hg_get_state");
     if (!c || !o) return HG_EINVAL;
     const int64_t n = c->n;
     struct F {
@@ -1068,6 +1094,7 @@ int hg_get_state(hg_ctx *c, hg_state *o)
 
 int hg_set_state(hg_ctx *c, const hg_state *in)
 {
+    const CallRange range_("hg_set_state");
     if (!c || !in) return HG_EINVAL;
     if (!in->mass || !in->pos || !in->vel || !in->acc || !in->jerk || !in->snap || !in->crackle || !in->t || !in->dt)
         return fail(c, HG_EINVAL, "every state field is required");
@@ -1115,6 +1142,7 @@ int hg_set_state(hg_ctx *c, const hg_state *in)
 
 int hg_bind_device(hg_ctx *c, const hg_state *dev, int copy_in)
 {
+    const CallRange range_("hg_bind_device");
     if (!c) return HG_EINVAL;
     const int64_t n = c->n;
     auto copy_state = [&](const State &dst, const State &src) -> int {
@@ -1202,6 +1230,7 @@ int hg_get_profile(hg_ctx *c, hg_profile *o, int reset)
 
 int hg_tune(hg_ctx *c, int64_t m_max, int32_t reps, hg_tune_entry *report, int32_t cap, int32_t *n_out)
 {
+    const CallRange range_("hg_tune");
     if (!c) return HG_EINVAL;
     if (reps < 0 || reps > 1000) return fail(c, HG_EINVAL, "reps must be in [0, 1000]");
     if (cap < 0 || (cap > 0 && !report)) return fail(c, HG_EINVAL, "report capacity without a report array");
@@ -1217,6 +1246,7 @@ int hg_tune(hg_ctx *c, int64_t m_max, int32_t reps, hg_tune_entry *report, int32
 
 int hg_time_evaluate(hg_ctx *c, const int32_t *idx, int64_t m, int32_t reps, double *us)
 {
+    const CallRange range_("hg_time_evaluate");
     if (!c || !us) return HG_EINVAL;
     if (isnan(c->t_pred)) return fail(c, HG_ESTATE, "hg_time_evaluate needs a preceding hg_predict");
     if (m < 1 || m > c->n || !idx) return fail(c, HG_EINVAL, "m must be in [1, n] and idx given");
@@ -1273,6 +1303,31 @@ int hg_set_tuning(hg_ctx *c, const int16_t *table)
     for (int k = 0; k < kTuneBuckets; ++k) c->pp.tuned[k] = table[k];
     drop_graphs(c);
     return HG_OK;
+}
+
+int hg_test_corrupt_list(hg_ctx *c, int64_t pos, int32_t value)
+{
+    if (!c) return HG_EINVAL;
+#if defined(HG_CHECKED)
+    const CallRange range_("hg_test_corrupt_list");
+    if (c->cur_m < 1 || pos < 0 || pos >= c->cur_m) return fail(c, HG_EINVAL, "pos must lie in the current block");
+    HG_CUDA(c, cudaMemcpyAsync(c->d_idx + pos, &value, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    HG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return HG_OK;
+#else
+    (void)pos;
+    (void)value;
+    return fail(c, HG_EINVAL, "hg_test_corrupt_list exists only in the checked build (HG_CHECKED)");
+#endif
+}
+
+int hg_build_checked(void)
+{
+#if defined(HG_CHECKED)
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 int hg_inject_fault(int32_t kind, int64_t nth)

@@ -497,6 +497,7 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
             nt64 = ntiles - tbase < tps ? ntiles - tbase : tps;
             rbase = split * m;
         }
+        if (!in_bounds(tbase >= 0 && nt64 >= 0 && tbase + nt64 <= args.npad / P::TJ, args.err)) nt64 = 0;
         const int nt = (int)nt64;
         const int lane_j = tid & (tpi - 1);
         const int slot = tid / tpi;
@@ -507,9 +508,13 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
 #pragma unroll
         for (int k = 0; k < P::I; ++k) {
             qi[k] = q_tile + (int64_t)slot * P::I + k;
-            const int64_t qc = qi[k] < q_end ? qi[k] : q_end - 1;
-            const int32_t i = args.idx[qc];
-            ids[k] = batch ? bv.rmap[i] : i;
+            int64_t qc = qi[k] < q_end ? qi[k] : q_end - 1;
+            if (!in_bounds(qc >= 0 && qc < args.n, args.err)) qc = 0;
+            int32_t i = args.idx[qc];
+            if (!in_bounds(i >= 0 && (int64_t)i < args.n, args.err)) i = 0;
+            int32_t r = batch ? bv.rmap[i] : i;
+            if (!in_bounds(r >= 0 && (int64_t)r < args.npad, args.err)) r = 0;
+            ids[k] = r;
         }
         P::load(args.rec, ids, iv);
         typename P::Acc acc;
@@ -565,7 +570,7 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
         if (lane_j == 0) {
 #pragma unroll
             for (int k = 0; k < P::I; ++k) {
-                if (qi[k] < q_end) {
+                if (qi[k] < q_end && in_bounds(rbase + qi[k] >= 0 && rbase + qi[k] < args.pcap, args.err)) {
                     double *dst = args.partial + (rbase + qi[k]) * kOut;
 #pragma unroll
                     for (int c = 0; c < kOut; ++c) dst[c] = out[k][c];
@@ -603,16 +608,20 @@ __global__ void k_reduce(const EvalArgs args, double *ra, double *rj, double *rs
              e += (int64_t)gridDim.x * blockDim.x) {
             const int64_t q = e / kOut;
             const int cv = (int)(e - q * kOut);
-            const int c = bv.cl_of[args.idx[q]];
+            const int32_t iq = args.idx[q];
+            if (!in_bounds(iq >= 0 && (int64_t)iq < args.n, args.err)) continue;
+            const int c = bv.cl_of[iq];
             const int64_t qb = bv.a_off[c], mc = bv.a_off[c + 1] - qb;
             const int64_t row0 = bv.part_off[c] + (q - qb);
             const int b = bv.b_c[c];
+            if (!in_bounds(row0 >= 0 && row0 + (int64_t)(b - 1) * mc < args.pcap, args.err)) continue;
             double s = 0.0;
             for (int sp = 0; sp < b; ++sp) s += args.partial[(row0 + (int64_t)sp * mc) * kOut + cv];
             put_result(args, ra, rj, rs, q, cv, s);
         }
         return;
     }
+    if (!in_bounds((int64_t)pl.b * m <= args.pcap, args.err)) return;
     if (pl.b <= 32) {
         // Few chunks: one thread per (particle, value), chunks in order.
         for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;

@@ -29,7 +29,7 @@ struct DevScalars {
                            // selection (the last one resets it); one spare
 };
 
-enum : int32_t { ERR_TIMEOUT = 1, ERR_BADIDX = 2, ERR_STATE = 4, ERR_VALUE = 8 };
+enum : int32_t { ERR_TIMEOUT = 1, ERR_BADIDX = 2, ERR_STATE = 4, ERR_VALUE = 8, ERR_BOUNDS = 16 };
 
 // FP64 state of every particle at its own time, structure of arrays.
 // tend = t + dt (exact: dyadic) is kept beside t and dt for the block selection.
@@ -262,6 +262,8 @@ constexpr int kOut = 10;
 struct EvalArgs {
     Records rec{};
     int64_t npad = 0;
+    int64_t n = 0;                     // particles (bounds of the active list's entries)
+    int64_t pcap = 0;                  // rows of the partial-sum buffer
     const int32_t *idx = nullptr;      // active list (device)
     const int64_t *m_dev = nullptr;    // block size on the device (graph mode), or nullptr
     int64_t m_host = 0;                // block size when m_dev == nullptr
@@ -384,6 +386,22 @@ __host__ __device__ __forceinline__ double f2d(float f)
 // PTX helpers: mbarrier and bulk (TMA) copies global -> shared.
 // ---------------------------------------------------------------------------
 #if defined(__CUDACC__)
+// Bounds check of the checked build (compiled with -DHG_CHECKED): a false
+// condition records ERR_BOUNDS in *err and the caller clamps or skips the
+// access, so an out-of-range index becomes a reported error instead of a
+// memory fault.  In the normal build the check compiles away (always true).
+__device__ __forceinline__ bool in_bounds(bool ok, int32_t *err)
+{
+#if defined(HG_CHECKED)
+    if (!ok) atomicOr(err, ERR_BOUNDS);
+    return ok;
+#else
+    (void)ok;
+    (void)err;
+    return true;
+#endif
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);

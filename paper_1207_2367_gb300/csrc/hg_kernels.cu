@@ -749,12 +749,13 @@ constexpr int kCorrUnit = 10;
 
 template <int P>
 __device__ __forceinline__ void correct_lane(const State &st, const int32_t *idx, const double *ra, const double *rj,
-                                             const double *rs, const double *rn, const StepParams &sp, int64_t m,
+                                             const double *rs, const double *rn, const StepParams &sp, int64_t m, int64_t n, int32_t *err,
                                              int64_t u, long long &low)
 {
     const int lane = threadIdx.x & 31, sub = lane / 3, k = lane - 3 * sub;
     const int64_t q = u * kCorrUnit + sub;
-    const bool act = sub < kCorrUnit && q < m;
+    bool act = sub < kCorrUnit && q < m;
+    if (act && !in_bounds(idx[q] >= 0 && (int64_t)idx[q] < n, err)) act = false;
     double dk[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, Ak = 0.0, h = 1.0;
     int64_t i = 0;
     int e = 0;
@@ -800,9 +801,9 @@ __global__ void __launch_bounds__(128) k_correct(State st, const int32_t *idx, c
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < units; u += nw) {   // warp-uniform
         if (sp.order == 4)
-            correct_lane<4>(st, idx, ra, rj, rs, rn, sp, m, u, low);
+            correct_lane<4>(st, idx, ra, rj, rs, rn, sp, m, n, &sc->err, u, low);
         else
-            correct_lane<6>(st, idx, ra, rj, rs, rn, sp, m, u, low);
+            correct_lane<6>(st, idx, ra, rj, rs, rn, sp, m, n, &sc->err, u, low);
     }
     if (!min_pass) return;
     // Next block time: min over the new tend of the particles corrected here and
@@ -1048,13 +1049,13 @@ __global__ void k_validate_idx(const int32_t *idx, int64_t m, int64_t n, int32_t
 
 // hg_correct preconditions: same list as the evaluation (when given) and every
 // listed particle due exactly at the prediction time.
-__global__ void k_check_correct(const State st, const int32_t *given, const int32_t *cur, int64_t m, double t_pred,
-                                int32_t *flag)
+__global__ void k_check_correct(const State st, const int32_t *given, const int32_t *cur, int64_t m, int64_t n,
+                                double t_pred, int32_t *flag)
 {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m; q += (int64_t)gridDim.x * blockDim.x) {
         const int32_t i = cur[q];
         bool ok = (given == nullptr) || (given[q] == i);
-        ok = ok && (st.t[i] + st.dt[i] == t_pred);
+        ok = ok && i >= 0 && (int64_t)i < n && (st.t[i] + st.dt[i] == t_pred);
         if (!ok) atomicOr(flag, ERR_STATE);
     }
 }
@@ -1413,10 +1414,10 @@ cudaError_t launch_validate_idx(const int32_t *idx, int64_t m, int64_t n, int32_
     return cudaGetLastError();
 }
 
-cudaError_t launch_check_correct(const State &st, const int32_t *given, const int32_t *cur, int64_t m, double t_pred,
-                                 int32_t *flag, cudaStream_t s)
+cudaError_t launch_check_correct(const State &st, const int32_t *given, const int32_t *cur, int64_t m, int64_t n,
+                                 double t_pred, int32_t *flag, cudaStream_t s)
 {
-    k_check_correct<<<grid_for(m, 256, 4096), 256, 0, s>>>(st, given, cur, m, t_pred, flag);
+    k_check_correct<<<grid_for(m, 256, 4096), 256, 0, s>>>(st, given, cur, m, n, t_pred, flag);
     return cudaGetLastError();
 }
 

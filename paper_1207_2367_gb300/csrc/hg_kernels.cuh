@@ -79,7 +79,7 @@ cudaError_t launch_validate_init(const double *mass, const double *x, const doub
 cudaError_t launch_validate_state(const State &st, int64_t n, double dt_min, double dt_max, const ValueLimits &lim,
                                   int32_t *flag, cudaStream_t s);
 cudaError_t launch_validate_idx(const int32_t *idx, int64_t m, int64_t n, int32_t *flag, cudaStream_t s);
-cudaError_t launch_check_correct(const State &st, const int32_t *given, const int32_t *cur, int64_t m, double t_pred,
-                                 int32_t *flag, cudaStream_t s);
+cudaError_t launch_check_correct(const State &st, const int32_t *given, const int32_t *cur, int64_t m, int64_t n,
+                                 double t_pred, int32_t *flag, cudaStream_t s);
 
 }  // namespace hg

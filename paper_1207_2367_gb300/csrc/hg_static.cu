@@ -219,6 +219,8 @@ extern "C" int hg_evaluate_static(int64_t n, const double *mass, const double *p
     a.bv = BatchView{};
     a.rec = rec;
     a.npad = npad;
+    a.n = n;
+    a.pcap = kStaticPcap;
     a.idx = idx;
     a.m_dev = nullptr;
     a.m_host = m;
@@ -244,6 +246,10 @@ extern "C" int hg_evaluate_static(int64_t n, const double *mass, const double *p
     if (hflags[0] & ERR_TIMEOUT) {
         set_call_error("a bounded device wait expired");
         return HG_ETIMEOUT;
+    }
+    if (hflags[0] & ERR_BOUNDS) {
+        set_call_error("a device bounds check failed (checked build)");
+        return HG_ECUDA;
     }
     return HG_OK;
 }
