@@ -48,11 +48,12 @@ FLOPS_F32 = 77     # FP32 adds + muls of the pair law per interaction (FMA = 2 f
 FLOPS_F64 = 77     # the same count for the FP64 path
 PAPER_FLOPS = 97   # the paper's count per interaction (82 SP + 15 DP)
 NUM_SMS = 152
-# DRAM bytes (read + write) of the evaluation kernel per launch (one per block
-# step) on the default workload, from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum, mean of 100 launches, cold L2).  Valid only while that
-# kernel is unchanged.
-EVAL_TRAFFIC = {(65536, "equal", "mixed"): 3.48e6}
+# DRAM bytes (read + write) of the evaluation kernel per launch, mean over the
+# timed launches of one bench configuration, from an ncu capture of exactly
+# those launches (dram__bytes_read.sum + dram__bytes_write.sum).  Keyed by
+# (N, masses, precision, warm-up steps, timed steps); valid only while that
+# kernel is unchanged (None: not captured for the current kernel).
+EVAL_TRAFFIC = {}
 
 # Workload of each mode: (n, imf, seed, eps, t_end); explicit flags override.
 MODE_DEFAULTS = {
@@ -423,7 +424,8 @@ def run_headline(a, rank, world, dist):
         ms_max, inter_tot = aggregate(ms, inter, dist, "cuda")
         value = inter_tot / (ms_max / 1e3)
         mhz, kind = sm_max_mhz()
-        roof = roofline(hg, inter, prof, True, mhz, kind, EVAL_TRAFFIC.get((a.n, a.imf, "mixed")), peaks)
+        roof = roofline(hg, inter, prof, True, mhz, kind, EVAL_TRAFFIC.get((a.n, a.imf, "mixed", a.warmup, a.steps)),
+                        peaks)
         roof["eval_ms_per_launch"] = prof["ms"]["evaluate"] / max(1, prof["block_steps"])
         roof["pairs_per_launch"] = inter / max(1, steps_taken)
         e2e = run_e2e_blocks(a, hg, ctx, bs) if (not a.no_e2e and rank == 0) else None
@@ -717,7 +719,7 @@ def run_interval(a, rank, world, dist):
                          "inputs resident in HBM",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline(hg, prof_inter, prof, mixed, mhz, kind,
-                             EVAL_TRAFFIC.get((a.n, a.imf, a.precision)) if a.block_steps == 0 else None),
+                             EVAL_TRAFFIC.get((a.n, a.imf, a.precision, a.warmup, a.steps)) if a.block_steps == 0 else None),
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,
