@@ -17,6 +17,7 @@
 #include <stdint.h>
 
 #include "hg_internal.cuh"
+#include "hg_step_dev.cuh"
 
 namespace hg {
 namespace {
@@ -43,6 +44,7 @@ struct Mixed {
     static constexpr int I = IPT;
     static constexpr int kMinBlocks = 3;
     static constexpr int kVariant = 0;
+    static constexpr bool kMixed = true;
     static constexpr uint32_t kStageBytes = TJ * 52;
     struct IData {
         f2_t xh, yh, zh, xl, yl, zl, vx, vy, vz, ax, ay, az;   // (v, v) duplicated
@@ -290,6 +292,7 @@ struct F64 {
     static constexpr int I = kIF64;
     static constexpr int kMinBlocks = 2;
     static constexpr int kVariant = 0;
+    static constexpr bool kMixed = false;
     static constexpr uint32_t kStageBytes = TJ * 80;
     struct IData {
         double x, y, z, vx, vy, vz, ax, ay, az;
@@ -304,11 +307,11 @@ struct F64 {
 
     __device__ static void load_i(const Records &rec, int i, IData &d)
     {
-        const double2 q0 = __ldg(static_cast<const double2 *>(rec.p[0]) + i);
-        const double2 q1 = __ldg(static_cast<const double2 *>(rec.p[1]) + i);
-        const double2 q2 = __ldg(static_cast<const double2 *>(rec.p[2]) + i);
-        const double2 q3 = __ldg(static_cast<const double2 *>(rec.p[3]) + i);
-        const double2 q4 = __ldg(static_cast<const double2 *>(rec.p[4]) + i);
+        const double2 q0 = __ldcg(static_cast<const double2 *>(rec.p[0]) + i);
+        const double2 q1 = __ldcg(static_cast<const double2 *>(rec.p[1]) + i);
+        const double2 q2 = __ldcg(static_cast<const double2 *>(rec.p[2]) + i);
+        const double2 q3 = __ldcg(static_cast<const double2 *>(rec.p[3]) + i);
+        const double2 q4 = __ldcg(static_cast<const double2 *>(rec.p[4]) + i);
         d.x = q0.x; d.y = q0.y; d.z = q1.x;
         d.vx = q2.x; d.vy = q2.y; d.vz = q3.x;
         d.ax = q3.y; d.ay = q4.x; d.az = q4.y;
@@ -436,33 +439,23 @@ constexpr size_t smem_bytes()
            (kEvalThreads / 32) * P::I * kOut * sizeof(double);
 }
 
+// The work items (i-tile, j-chunk) of one evaluation that this CTA takes
+// (items blockIdx.x, blockIdx.x + gridDim.x, ...): the body of k_eval and the
+// evaluation phase of the fused block-step kernel.  bars: the kStages
+// initialised mbarriers of the tile ring; seq: tiles this CTA consumed so far
+// (their phase bookkeeping, carried across calls).  False when a bounded wait
+// expired (ERR_TIMEOUT is set; the copies in flight have been waited for).
 template <class P, bool GUARD>
-__global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const EvalArgs args)
+__device__ bool eval_items(const EvalArgs &args, int64_t m, const Plan &pl, unsigned char *smem, uint64_t *bars,
+                           double *red, uint32_t &seq)
 {
-    extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * P::kStageBytes);
-    double *red = reinterpret_cast<double *>(bars + kStages);
     const int tid = threadIdx.x;
-
-    const int64_t m = args.m_dev ? *args.m_dev : args.m_host;
-    if (m <= 0) return;
     const BatchView &bv = args.bv;
     const bool batch = bv.nc > 0;
-    const Plan pl = args.plan_dev ? *args.plan_dev : args.plan_host;
-    if (!batch && pl.variant != P::kVariant) return;   // a plan for another kernel (none at present)
+    if (!batch && pl.variant != P::kVariant) return true;   // a plan for another kernel (none at present)
     const int64_t n_items = batch ? bv.item_off[bv.nc] : pl.n_items;
     const int64_t tps = batch ? *bv.tps : pl.tiles_per_split;
-    if ((int64_t)blockIdx.x >= n_items) return;
-
-    if (tid == 0) {
-#pragma unroll
-        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-
     const typename P::Eps eps2 = (typename P::Eps)args.eps2;
-    uint32_t seq = 0;   // tiles consumed so far by this CTA (mbarrier phase bookkeeping)
 
     for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
         // Decode the item: active positions [q_begin, q_end) of this i-tile's
@@ -512,7 +505,7 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
             qi[k] = q_tile + (int64_t)slot * P::I + k;
             int64_t qc = qi[k] < q_end ? qi[k] : q_end - 1;
             if (!in_bounds(qc >= 0 && qc < args.n, args.err)) qc = 0;
-            int32_t i = args.idx[qc];
+            int32_t i = __ldcg(args.idx + qc);
             if (!in_bounds(i >= 0 && (int64_t)i < args.n, args.err)) i = 0;
             int32_t r = batch ? bv.rmap[i] : i;
             if (!in_bounds(r >= 0 && (int64_t)r < args.npad, args.err)) r = 0;
@@ -543,7 +536,7 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
                         mbar_wait_bounded(&bars[q % kStages], (q / kStages) & 1u, args.err);
                     }
                 }
-                return;
+                return false;
             }
             if (tid == 0 && t + kStages < nt) {
                 fence_proxy_async();
@@ -580,6 +573,28 @@ __global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const Eval
             }
         }
     }
+    return true;
+}
+
+template <class P, bool GUARD>
+__global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_eval(const EvalArgs args)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * P::kStageBytes);
+    double *red = reinterpret_cast<double *>(bars + kStages);
+    const int64_t m = args.m_dev ? *args.m_dev : args.m_host;
+    if (m <= 0) return;
+    const Plan pl = args.plan_dev ? *args.plan_dev : args.plan_host;
+    const int64_t n_items = args.bv.nc > 0 ? args.bv.item_off[args.bv.nc] : pl.n_items;
+    if ((int64_t)blockIdx.x >= n_items) return;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t seq = 0;   // tiles consumed so far by this CTA (mbarrier phase bookkeeping)
+    eval_items<P, GUARD>(args, m, pl, smem, bars, red, seq);
 }
 
 // Table 1 section 4: sum the b j-chunk partials of every listed particle in
@@ -596,21 +611,21 @@ __device__ __forceinline__ void put_result(const EvalArgs &a, double *ra, double
     dst[q * 3 + (c % 3)] = v;
 }
 
-__global__ void k_reduce(const EvalArgs args, double *ra, double *rj, double *rs)
+// The reduction's values taken by global thread g of G threads (grid-stride):
+// the body of k_reduce and the reduction phase of the fused block-step kernel.
+// Each (particle, value) sum has a fixed order whichever thread takes it.
+__device__ void reduce_values(const EvalArgs &args, int64_t m, const Plan &pl, double *ra, double *rj, double *rs,
+                              int64_t g, int64_t G)
 {
-    const int64_t m = args.m_dev ? *args.m_dev : args.m_host;
-    if (m <= 0) return;
-    const Plan pl = args.plan_dev ? *args.plan_dev : args.plan_host;
     if (args.bv.nc == 0 && args.direct_b1 && pl.b == 1) return;   // the evaluation wrote the results
     const int64_t total = m * kOut;
     if (args.bv.nc > 0) {
         // Clusters: the chunks of position q are rows part_off[c] + s * m_c + (q - a_off[c]).
         const BatchView &bv = args.bv;
-        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-             e += (int64_t)gridDim.x * blockDim.x) {
+        for (int64_t e = g; e < total; e += G) {
             const int64_t q = e / kOut;
             const int cv = (int)(e - q * kOut);
-            const int32_t iq = args.idx[q];
+            const int32_t iq = __ldcg(args.idx + q);
             if (!in_bounds(iq >= 0 && (int64_t)iq < args.n, args.err)) continue;
             const int c = bv.cl_of[iq];
             const int64_t qb = bv.a_off[c], mc = bv.a_off[c + 1] - qb;
@@ -618,7 +633,7 @@ __global__ void k_reduce(const EvalArgs args, double *ra, double *rj, double *rs
             const int b = bv.b_c[c];
             if (!in_bounds(row0 >= 0 && row0 + (int64_t)(b - 1) * mc < args.pcap, args.err)) continue;
             double s = 0.0;
-            for (int sp = 0; sp < b; ++sp) s += args.partial[(row0 + (int64_t)sp * mc) * kOut + cv];
+            for (int sp = 0; sp < b; ++sp) s += __ldcg(args.partial + (row0 + (int64_t)sp * mc) * kOut + cv);
             put_result(args, ra, rj, rs, q, cv, s);
         }
         return;
@@ -626,35 +641,146 @@ __global__ void k_reduce(const EvalArgs args, double *ra, double *rj, double *rs
     if (!in_bounds((int64_t)pl.b * m <= args.pcap, args.err)) return;
     if (pl.b <= 32) {
         // Few chunks: one thread per (particle, value), chunks in order.
-        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-             e += (int64_t)gridDim.x * blockDim.x) {
+        for (int64_t e = g; e < total; e += G) {
             const int64_t q = e / kOut;
             const int c = (int)(e - q * kOut);
             double s = 0.0;
-            for (int sp = 0; sp < pl.b; ++sp) s += args.partial[((int64_t)sp * m + q) * kOut + c];
+            for (int sp = 0; sp < pl.b; ++sp) s += __ldcg(args.partial + ((int64_t)sp * m + q) * kOut + c);
             put_result(args, ra, rj, rs, q, c, s);
         }
     } else {
         // Many chunks (small blocks): one warp per (particle, value); lane l
         // sums chunks l, l+32, ..., then a fixed butterfly combines the lanes.
-        const int lane = threadIdx.x & 31;
-        const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-        const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        const int lane = (int)(g & 31);
+        const int64_t wid = g >> 5;
+        const int64_t nw = G >> 5;
         for (int64_t e = wid; e < total; e += nw) {
             const int64_t q = e / kOut;
             const int c = (int)(e - q * kOut);
             double s = 0.0;
-            for (int sp = lane; sp < pl.b; sp += 32) s += args.partial[((int64_t)sp * m + q) * kOut + c];
+            for (int sp = lane; sp < pl.b; sp += 32) s += __ldcg(args.partial + ((int64_t)sp * m + q) * kOut + c);
             for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
             if (lane == 0) put_result(args, ra, rj, rs, q, c, s);
         }
     }
 }
 
+__global__ void k_reduce(const EvalArgs args, double *ra, double *rj, double *rs)
+{
+    const int64_t m = args.m_dev ? *args.m_dev : args.m_host;
+    if (m <= 0) return;
+    const Plan pl = args.plan_dev ? *args.plan_dev : args.plan_host;
+    reduce_values(args, m, pl, ra, rj, rs, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                  (int64_t)gridDim.x * blockDim.x);
+}
+
+// Fused block steps (one system, cooperative launch: every CTA resident).  Each
+// step: (1) select and predict (Table 1 sections 1-2) -> barrier -> the plan
+// for m, formed by every CTA (the device planner's choice) -> (2) evaluate the
+// plan's work items -> barrier -> (3) sum the j-split partials -> barrier ->
+// (4) correct, take the new steps and the next block time -> barrier.  No
+// kernel boundary, launch or last-CTA election between the passes; a bounded
+// barrier wait that runs out sets ERR_TIMEOUT and every CTA leaves.
+template <class P, bool GUARD>
+__global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_fused_steps(const FusedArgs fa)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * P::kStageBytes);
+    double *red = reinterpret_cast<double *>(bars + kStages);
+    __shared__ Plan s_plan;
+    __shared__ long long s_min[32];
+    DevScalars *sc = fa.sc;
+    int32_t *err = &sc->err;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t seq = 0;   // tiles consumed so far by this CTA (mbarrier phases, across steps)
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t G = (int64_t)gridDim.x * blockDim.x;
+    for (int step = 0; step < fa.steps; ++step) {
+        const long long tn = *((volatile long long *)&sc->tnext_bits);
+        const double t_next = __longlong_as_double(tn);
+        if (!(t_next <= *((volatile double *)&sc->t_stop))) {
+            // Past the stop time: no step (m = 0, done).  Every CTA read the same
+            // values after the last barrier, so every CTA leaves here.
+            if (g == 0) {
+                sc->m = 0;
+                sc->done = 1;
+            }
+            return;
+        }
+        predict_select_pass<P::kMixed>(fa.st, fa.ev.rec, fa.n, fa.npad, fa.idx, sc, tn, g, G);
+        if (!grid_sync(&sc->bar_count, &sc->bar_gen, err)) return;   // list, its size, records
+        const int64_t m = (int64_t)*((volatile uint32_t *)&sc->slot);
+        plan_on_block(m > 0 ? m : 1, fa.pq, &s_plan);
+        __syncthreads();
+        const Plan pl = s_plan;
+        if (g == 0) {
+            sc->m = m;
+            sc->t_cur = t_next;
+            sc->done = 0;
+            sc->steps += 1;
+            sc->interactions += m * fa.n;
+            *reinterpret_cast<Plan *>(sc->plan) = pl;
+            sc->tnext_bits = LLONG_MAX;   // every CTA has read it; the correction's minimum goes here
+        }
+        if (m > 0 && !eval_items<P, GUARD>(fa.ev, m, pl, smem, bars, red, seq)) return;
+        if (!grid_sync(&sc->bar_count, &sc->bar_gen, err)) return;   // partial sums
+        if (g == 0) sc->slot = 0u;                                     // every CTA has read m
+        if (m > 0) reduce_values(fa.ev, m, pl, fa.ev.ra, fa.ev.rj, fa.ev.rs, g, G);
+        if (!grid_sync(&sc->bar_count, &sc->bar_gen, err)) return;   // acc, jerk, snap, noise scale
+        if (m > 0) {
+            long long low = LLONG_MAX;
+            correct_pass(fa.st, fa.idx, m, fa.n, fa.ev.ra, fa.ev.rj, fa.ev.rs, fa.ev.rn, fa.sp, err, g >> 5, G >> 5,
+                         low);
+            next_min_pass(fa.st, fa.n, sc, tn, g, G, low, s_min);
+        }
+        if (!grid_sync(&sc->bar_count, &sc->bar_gen, err)) return;   // new state, next block time
+    }
+}
+
 template <class P, bool G>
 cudaError_t set_attr()
 {
-    return cudaFuncSetAttribute(k_eval<P, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<P>());
+    cudaError_t e = cudaFuncSetAttribute(k_eval<P, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<P>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_fused_steps<P, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes<P>());
+}
+
+template <class P, bool G>
+int fused_grid_of(int device, int num_sms)
+{
+    int coop = 0, nb = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fused_steps<P, G>, kEvalThreads, smem_bytes<P>()) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb * num_sms;
+}
+
+template <class P, bool G>
+cudaError_t launch_fused_of(const FusedArgs &fa, int grid, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kEvalThreads);
+    cfg.dynamicSmemBytes = smem_bytes<P>();
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_fused_steps<P, G>, fa);
 }
 
 template <class P, bool G>
@@ -705,6 +831,19 @@ int clip_grid(const EvalArgs &args, int num_sms)
 }  // namespace
 
 int eval_launches(bool, const EvalArgs &) { return 1; }
+
+int fused_grid(bool mixed, bool guard, int device, int num_sms)
+{
+    if (mixed) return guard ? fused_grid_of<MixedEval, true>(device, num_sms) : fused_grid_of<MixedEval, false>(device, num_sms);
+    return guard ? fused_grid_of<F64, true>(device, num_sms) : fused_grid_of<F64, false>(device, num_sms);
+}
+
+cudaError_t launch_fused_steps(bool mixed, const FusedArgs &fa, int grid, cudaStream_t st)
+{
+    if (mixed)
+        return fa.ev.guard ? launch_fused_of<MixedEval, true>(fa, grid, st) : launch_fused_of<MixedEval, false>(fa, grid, st);
+    return fa.ev.guard ? launch_fused_of<F64, true>(fa, grid, st) : launch_fused_of<F64, false>(fa, grid, st);
+}
 
 cudaError_t launch_eval(bool mixed, const EvalArgs &args, int num_sms, cudaStream_t st)
 {

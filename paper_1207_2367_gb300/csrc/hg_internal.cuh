@@ -27,6 +27,8 @@ struct DevScalars {
     int64_t tnext_bits;    // bit pattern of min_i tend_i (next-block pass 1, or the last correction)
     uint32_t arrive[4];    // CTAs done in next-block passes 1 and 2 and in the fused
                            // selection (the last one resets it); one spare
+    uint32_t bar_count;    // grid barrier of the fused block-step kernel: arrivals
+    uint32_t bar_gen;      //   and generation
 };
 
 enum : int32_t { ERR_TIMEOUT = 1, ERR_BADIDX = 2, ERR_STATE = 4, ERR_VALUE = 8, ERR_BOUNDS = 16 };
@@ -493,13 +495,13 @@ __device__ __forceinline__ MixedRecord load_mixed_record(const Records &rec, int
     const int64_t b = (r >> 1) * 4 + (r & 1);
     const float *const *a = reinterpret_cast<const float *const *>(rec.p);
     MixedRecord v;
-    v.xh = __ldg(a[0] + b); v.yh = __ldg(a[0] + b + 2);
-    v.zh = __ldg(a[1] + b); v.m = __ldg(a[1] + b + 2);
-    v.xl = __ldg(a[2] + b); v.yl = __ldg(a[2] + b + 2);
-    v.zl = __ldg(a[3] + b); v.ax = __ldg(a[3] + b + 2);
-    v.vx = __ldg(a[4] + b); v.vy = __ldg(a[4] + b + 2);
-    v.vz = __ldg(a[5] + b); v.ay = __ldg(a[5] + b + 2);
-    v.az = __ldg(a[6] + (r >> 1) * 2 + (r & 1));
+    v.xh = __ldcg(a[0] + b); v.yh = __ldcg(a[0] + b + 2);
+    v.zh = __ldcg(a[1] + b); v.m = __ldcg(a[1] + b + 2);
+    v.xl = __ldcg(a[2] + b); v.yl = __ldcg(a[2] + b + 2);
+    v.zl = __ldcg(a[3] + b); v.ax = __ldcg(a[3] + b + 2);
+    v.vx = __ldcg(a[4] + b); v.vy = __ldcg(a[4] + b + 2);
+    v.vz = __ldcg(a[5] + b); v.ay = __ldcg(a[5] + b + 2);
+    v.az = __ldcg(a[6] + (r >> 1) * 2 + (r & 1));
     return v;
 }
 
