@@ -111,7 +111,7 @@ def parse():
                          "and angular-momentum errors against eta (N = 16384, both paths); jsplit: evaluation "
                          "rate against m at N_j = 16384 with the j-split forced off and on (Sect. 5.5 Bfactor); "
                          "step-times: device time of every block step from t = 0 to --t-end, one graph replay each, "
-                         "fused block-step kernel against the separate kernels (no section events)")
+                         "no section events")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the cost model's launch plans (no hg_tune before the warm-up)")
     a = ap.parse_args()
@@ -584,10 +584,9 @@ def run_step_times(a):
     """Device time of every block step of the integration from t = 0 to --t-end
     (default 1/8) on the Plummer sphere of --n particles (default 65536), each
     step one graph replay (hg_step(ctx, 1)) between CUDA events on the context's
-    stream, without section events: the fused block-step kernel (one cooperative
-    launch per replay) against the four separate kernels, both precisions, with
-    the cost model's plans.  Per power-of-two bucket of m: steps, mean m, median
-    and mean step time; and the whole run's device time."""
+    stream, without section events, both precisions, cost-model plans.  Per
+    power-of-two bucket of m: steps, mean m, median and mean step time; and the
+    whole run's device time."""
     import torch
     from paper_1207_2367_gb300 import binding as hg
     from paper_1207_2367_gb300 import inputs
@@ -596,43 +595,40 @@ def run_step_times(a):
     hg.load()
     stream = torch.cuda.Stream()
     p = inputs.plummer(a.n, a.seed, imf=a.imf)
-    out = {"metric": "device time per block step, fused kernel vs separate kernels", "unit": "us",
+    out = {"metric": "device time per block step (graph replay, no section events)", "unit": "us",
            "config": {"workload": f"Plummer N={a.n}, {a.imf} masses (seed {a.seed}), eps={a.eps:g}, eta=0.45, "
                                   f"dt_max=1/16, t = 0 -> {a.t_end:g}, every block step, one graph replay each"}}
     wanted = {"fp64": hg.HG_FP64, "mixed": hg.HG_MIXED}
     for name in [x for x in a.precisions.split(",") if x]:
-        res = {}
-        for arm, fused in (("fused", 1), ("separate", -1)):
-            o = hg.hg_default_opts(precision=wanted[name], dt_max=1.0 / 16, stream=stream, fused_steps=fused)
-            ctx = hg.hg_init(p.mass, p.pos, p.vel, a.eps, 0.45, o)
-            try:
-                hg.hg_step(ctx, 1)                  # graphs captured, first replay
-                rows, total = [], 0.0
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                while True:
-                    q0 = hg.hg_get_stats(ctx)
-                    if q0["t_sys"] >= a.t_end:
-                        break
-                    e0.record(stream)
-                    hg.hg_step(ctx, 1)
-                    e1.record(stream)
-                    e1.synchronize()
-                    us = 1e3 * e0.elapsed_time(e1)
-                    total += us
-                    rows.append(((hg.hg_get_stats(ctx)["interactions"] - q0["interactions"]) // a.n, us))
-            finally:
-                hg.hg_free(ctx)
-            buckets = {}
-            for m, us in rows:
-                buckets.setdefault(max(1, m).bit_length() - 1, []).append((m, us))
-            table = []
-            for k in sorted(buckets):
-                ms = np.array([x[0] for x in buckets[k]])
-                ts = np.array([x[1] for x in buckets[k]])
-                table.append({"bucket": f"[{1 << k}, {(2 << k) - 1}]", "steps": len(ts), "mean_m": float(ms.mean()),
-                              "median_us": float(np.median(ts)), "mean_us": float(ts.mean())})
-            res[arm] = {"buckets": table, "total_ms": total / 1e3, "block_steps": len(rows)}
-        out[name] = res
+        o = hg.hg_default_opts(precision=wanted[name], dt_max=1.0 / 16, stream=stream)
+        ctx = hg.hg_init(p.mass, p.pos, p.vel, a.eps, 0.45, o)
+        try:
+            hg.hg_step(ctx, 1)                  # graphs captured, first replay
+            rows, total = [], 0.0
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            while True:
+                q0 = hg.hg_get_stats(ctx)
+                if q0["t_sys"] >= a.t_end:
+                    break
+                e0.record(stream)
+                hg.hg_step(ctx, 1)
+                e1.record(stream)
+                e1.synchronize()
+                us = 1e3 * e0.elapsed_time(e1)
+                total += us
+                rows.append(((hg.hg_get_stats(ctx)["interactions"] - q0["interactions"]) // a.n, us))
+        finally:
+            hg.hg_free(ctx)
+        buckets = {}
+        for m, us in rows:
+            buckets.setdefault(max(1, m).bit_length() - 1, []).append((m, us))
+        table = []
+        for k in sorted(buckets):
+            ms = np.array([x[0] for x in buckets[k]])
+            ts = np.array([x[1] for x in buckets[k]])
+            table.append({"bucket": f"[{1 << k}, {(2 << k) - 1}]", "steps": len(ts), "mean_m": float(ms.mean()),
+                          "median_us": float(np.median(ts)), "mean_us": float(ts.mean())})
+        out[name] = {"buckets": table, "total_ms": total / 1e3, "block_steps": len(rows)}
     print(json.dumps(out), flush=True)
 
 

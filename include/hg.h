@@ -64,15 +64,6 @@ typedef struct hg_opts {
                                  Hermite scheme; 4 is the 4th-order Hermite scheme its step criterion
                                  admits with p = 4 (corrector from a and jerk, snap and crackle from the
                                  cubic interpolant; stored snap and crackle stay zero) */
-    int32_t fused_steps;      /* graph-replayed block steps of one system (hg_step, hg_advance):
-                                 0 = automatic (fused when n <= 262144 and profile = 0), 1 = fused,
-                                 -1 = separate kernels.  Fused: one cooperative launch runs all the
-                                 block steps of a graph, the passes (selection and prediction,
-                                 evaluation, reduction, correction) separated by grid-wide barriers
-                                 instead of kernel boundaries, with the same device code and launch
-                                 plans, so the results are bitwise those of the separate kernels.
-                                 1 needs one system, n <= 1048576 and profile = 0 (HG_EINVAL
-                                 otherwise) */
     double dt_min;            /* smallest step, power of two (default 2^-25, Sect. 3) */
     double dt_max;            /* largest step, power of two (default 2^-3, Sect. 3) */
     double eta_init;          /* accuracy parameter of the first step (p = 4 criterion; default 0.01) */

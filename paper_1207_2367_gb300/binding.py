@@ -32,7 +32,7 @@ class hg_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("energy_precision", C.c_int32), ("device", C.c_int32),
                 ("tpi", C.c_int32), ("jsplit", C.c_int32), ("graph_steps", C.c_int32),
                 ("start_mode", C.c_int32), ("profile", C.c_int32),
-                ("test_stall_eval", C.c_int32), ("order", C.c_int32), ("fused_steps", C.c_int32),
+                ("test_stall_eval", C.c_int32), ("order", C.c_int32),
                 ("dt_min", C.c_double), ("dt_max", C.c_double), ("eta_init", C.c_double),
                 ("stream", C.c_void_p)]
 

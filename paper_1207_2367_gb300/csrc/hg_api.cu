@@ -56,8 +56,6 @@ struct hg_ctx {
     double prof_ms[5] = {0, 0, 0, 0, 0};
     int64_t prof_steps = 0;
     bool tnext_valid = false;   // d_sc->tnext_bits = min_i tend_i of the current state
-    bool fused = false;         // graph steps run the fused block-step kernel
-    int fused_grid = 0;         // its CTAs (all resident)
     double t_pred = NAN;    // time of the last hg_predict (NaN: none valid)
     int64_t cur_m = -1;     // size of the block from hg_next_block (-1: none)
     int64_t eval_m = -1;    // size of the last hg_evaluate (-1: none pending)
@@ -277,25 +275,7 @@ int upload_scalar(hg_ctx *c, double *dev_field, double v)
 // Kernels per graph-replayed block step: one system, selection + prediction,
 // evaluation, reduction, correction (with the next minimum); clusters, three
 // next-block passes, batch plan, prediction, evaluation, reduction, correction.
-// (The fused kernel runs all the steps of a graph in one launch.)
 int step_kernels(const hg_ctx *c) { return c->bv.nc > 0 ? 8 : 4; }
-
-// The fused kernel's arguments: the graph path's evaluation arguments (m and
-// the plan are formed in the kernel) and the correction's.
-FusedArgs fused_args(hg_ctx *c, int steps)
-{
-    FusedArgs f;
-    f.ev = eval_args(c, &c->d_sc->m, 0);
-    f.idx = c->d_idx;
-    f.st = c->st;
-    f.n = c->n;
-    f.npad = c->npad;
-    f.sc = c->d_sc;
-    f.pq = c->pp;
-    f.sp = step_params(c);
-    f.steps = steps;
-    return f;
-}
 
 // An event record that becomes a graph node when the stream is being captured
 // (a plain record inside a capture only orders work and cannot be timed).
@@ -355,11 +335,7 @@ int capture(hg_ctx *c, int steps, cudaGraphExec_t *out, std::vector<cudaEvent_t>
     }
     HG_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = HG_OK;
-    if (c->fused) {
-        const cudaError_t e = launch_fused_steps(c->mixed, fused_args(c, steps), c->fused_grid, c->cap_stream);
-        if (e != cudaSuccess) rc = fail(c, HG_ECUDA, std::string("fused block steps: ") + cudaGetErrorString(e));
-    }
-    for (int k = 0; k < steps && rc == HG_OK && !c->fused; ++k)
+    for (int k = 0; k < steps && rc == HG_OK; ++k)
         rc = enqueue_block_step(c, c->cap_stream, c->opts.profile ? &ev[(size_t)k * 6] : nullptr);
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
     if (rc != HG_OK) {
@@ -386,7 +362,7 @@ int replay(hg_ctx *c, bool many)
 {
     HG_CUDA(c, cudaGraphLaunch(many ? c->g_many : c->g_one, c->stream));
     const int steps = many ? c->opts.graph_steps : 1;
-    c->kernels += c->fused ? 1 : (int64_t)step_kernels(c) * steps;
+    c->kernels += (int64_t)step_kernels(c) * steps;
     if (!c->opts.profile) return HG_OK;
     HG_CUDA(c, cudaStreamSynchronize(c->stream));
     const std::vector<cudaEvent_t> &ev = many ? c->ev_many : c->ev_one;
@@ -556,20 +532,6 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
     HG_CUDA(c, eval_setup(c->device));
     c->pp = plan_params(c->mixed, c->npad, c->num_sms, c->pcap, c->opts.tpi, c->opts.jsplit);
     if (nc > 0) c->pp.variants = 1;   // the cluster work list is built for the first kernel variant
-    // Fused graph steps: one system, no section profile, and (automatic) small
-    // enough that no pass of a block step approaches the bounded barrier wait.
-    const bool can_fuse = nc == 0 && c->opts.profile == 0;
-    if (c->opts.fused_steps == 1 || (c->opts.fused_steps == 0 && can_fuse && n <= (1 << 18))) {
-        if (!can_fuse || n > (1 << 20))
-            return fail(c, HG_EINVAL, "fused_steps = 1 needs one system, n <= 1048576 and profile = 0");
-        c->fused_grid = fused_grid(c->mixed, c->eps == 0.0, c->device, c->num_sms);
-        if (c->fused_grid <= 0) {
-            if (c->opts.fused_steps == 1)
-                return fail(c, HG_ECUDA, "the fused block-step kernel cannot be launched cooperatively here");
-        } else {
-            c->fused = true;
-        }
-    }
 
     DevScalars z{};
     z.t_stop = INFINITY;
@@ -793,7 +755,6 @@ void hg_default_opts(hg_opts *o)
     o->profile = 0;
     o->test_stall_eval = 0;
     o->order = 6;
-    o->fused_steps = 0;
     o->dt_min = 1.0 / 33554432.0;   // 2^-25
     o->dt_max = 0.125;              // 2^-3
     o->eta_init = 0.01;
@@ -854,7 +815,6 @@ int hg_init_batch(hg_ctx **out, int32_t n_clusters, const int64_t *offsets, int6
     if (o.test_stall_eval != 0 && o.test_stall_eval != 1) return bad("test_stall_eval must be 0 or 1");
     if (o.order == 0) o.order = 6;
     if (o.order != 4 && o.order != 6) return bad("order must be 4 or 6");
-    if (o.fused_steps < -1 || o.fused_steps > 1) return bad("fused_steps must be -1, 0 or 1");
 
     hg_ctx *c = new (std::nothrow) hg_ctx();
     if (!c) {

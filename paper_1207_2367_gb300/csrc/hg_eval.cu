@@ -17,7 +17,6 @@
 #include <stdint.h>
 
 #include "hg_internal.cuh"
-#include "hg_step_dev.cuh"
 
 namespace hg {
 namespace {
@@ -44,7 +43,6 @@ struct Mixed {
     static constexpr int I = IPT;
     static constexpr int kMinBlocks = 3;
     static constexpr int kVariant = 0;
-    static constexpr bool kMixed = true;
     static constexpr uint32_t kStageBytes = TJ * 52;
     struct IData {
         f2_t xh, yh, zh, xl, yl, zl, vx, vy, vz, ax, ay, az;   // (v, v) duplicated
@@ -292,7 +290,6 @@ struct F64 {
     static constexpr int I = kIF64;
     static constexpr int kMinBlocks = 2;
     static constexpr int kVariant = 0;
-    static constexpr bool kMixed = false;
     static constexpr uint32_t kStageBytes = TJ * 80;
     struct IData {
         double x, y, z, vx, vy, vz, ax, ay, az;
@@ -674,113 +671,10 @@ __global__ void k_reduce(const EvalArgs args, double *ra, double *rj, double *rs
                   (int64_t)gridDim.x * blockDim.x);
 }
 
-// Fused block steps (one system, cooperative launch: every CTA resident).  Each
-// step: (1) select and predict (Table 1 sections 1-2) -> barrier -> the plan
-// for m, formed by every CTA (the device planner's choice) -> (2) evaluate the
-// plan's work items -> barrier -> (3) sum the j-split partials -> barrier ->
-// (4) correct, take the new steps and the next block time -> barrier.  No
-// kernel boundary, launch or last-CTA election between the passes; a bounded
-// barrier wait that runs out sets ERR_TIMEOUT and every CTA leaves.
-template <class P, bool GUARD>
-__global__ void __launch_bounds__(kEvalThreads, P::kMinBlocks) k_fused_steps(const FusedArgs fa)
-{
-    extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * P::kStageBytes);
-    double *red = reinterpret_cast<double *>(bars + kStages);
-    __shared__ Plan s_plan;
-    __shared__ long long s_min[32];
-    DevScalars *sc = fa.sc;
-    int32_t *err = &sc->err;
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    uint32_t seq = 0;   // tiles consumed so far by this CTA (mbarrier phases, across steps)
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t G = (int64_t)gridDim.x * blockDim.x;
-    for (int step = 0; step < fa.steps; ++step) {
-        const long long tn = *((volatile long long *)&sc->tnext_bits);
-        const double t_next = __longlong_as_double(tn);
-        if (!(t_next <= *((volatile double *)&sc->t_stop))) {
-            // Past the stop time: no step (m = 0, done).  Every CTA read the same
-            // values after the last barrier, so every CTA leaves here.
-            if (g == 0) {
-                sc->m = 0;
-                sc->done = 1;
-            }
-            return;
-        }
-        predict_select_pass<P::kMixed>(fa.st, fa.ev.rec, fa.n, fa.npad, fa.idx, sc, tn, g, G);
-        if (!grid_sync(&sc->bar_count, &sc->bar_gen, err)) return;   // list, its size, records
-        const int64_t m = (int64_t)*((volatile uint32_t *)&sc->slot);
-        plan_on_block(m > 0 ? m : 1, fa.pq, &s_plan);
-        __syncthreads();
-        const Plan pl = s_plan;
-        if (g == 0) {
-            sc->m = m;
-            sc->t_cur = t_next;
-            sc->done = 0;
-            sc->steps += 1;
-            sc->interactions += m * fa.n;
-            *reinterpret_cast<Plan *>(sc->plan) = pl;
-            sc->tnext_bits = LLONG_MAX;   // every CTA has read it; the correction's minimum goes here
-        }
-        if (m > 0 && !eval_items<P, GUARD>(fa.ev, m, pl, smem, bars, red, seq)) return;
-        if (!grid_sync(&sc->bar_count, &sc->bar_gen, err)) return;   // partial sums
-        if (g == 0) sc->slot = 0u;                                     // every CTA has read m
-        if (m > 0) reduce_values(fa.ev, m, pl, fa.ev.ra, fa.ev.rj, fa.ev.rs, g, G);
-        if (!grid_sync(&sc->bar_count, &sc->bar_gen, err)) return;   // acc, jerk, snap, noise scale
-        if (m > 0) {
-            long long low = LLONG_MAX;
-            correct_pass(fa.st, fa.idx, m, fa.n, fa.ev.ra, fa.ev.rj, fa.ev.rs, fa.ev.rn, fa.sp, err, g >> 5, G >> 5,
-                         low);
-            next_min_pass(fa.st, fa.n, sc, tn, g, G, low, s_min);
-        }
-        if (!grid_sync(&sc->bar_count, &sc->bar_gen, err)) return;   // new state, next block time
-    }
-}
-
 template <class P, bool G>
 cudaError_t set_attr()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_eval<P, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<P>());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_fused_steps<P, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes<P>());
-}
-
-template <class P, bool G>
-int fused_grid_of(int device, int num_sms)
-{
-    int coop = 0, nb = 0;
-    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop) {
-        cudaGetLastError();
-        return 0;
-    }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fused_steps<P, G>, kEvalThreads, smem_bytes<P>()) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    return nb * num_sms;
-}
-
-template <class P, bool G>
-cudaError_t launch_fused_of(const FusedArgs &fa, int grid, cudaStream_t st)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(kEvalThreads);
-    cfg.dynamicSmemBytes = smem_bytes<P>();
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_fused_steps<P, G>, fa);
+    return cudaFuncSetAttribute(k_eval<P, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<P>());
 }
 
 template <class P, bool G>
@@ -831,19 +725,6 @@ int clip_grid(const EvalArgs &args, int num_sms)
 }  // namespace
 
 int eval_launches(bool, const EvalArgs &) { return 1; }
-
-int fused_grid(bool mixed, bool guard, int device, int num_sms)
-{
-    if (mixed) return guard ? fused_grid_of<MixedEval, true>(device, num_sms) : fused_grid_of<MixedEval, false>(device, num_sms);
-    return guard ? fused_grid_of<F64, true>(device, num_sms) : fused_grid_of<F64, false>(device, num_sms);
-}
-
-cudaError_t launch_fused_steps(bool mixed, const FusedArgs &fa, int grid, cudaStream_t st)
-{
-    if (mixed)
-        return fa.ev.guard ? launch_fused_of<MixedEval, true>(fa, grid, st) : launch_fused_of<MixedEval, false>(fa, grid, st);
-    return fa.ev.guard ? launch_fused_of<F64, true>(fa, grid, st) : launch_fused_of<F64, false>(fa, grid, st);
-}
 
 cudaError_t launch_eval(bool mixed, const EvalArgs &args, int num_sms, cudaStream_t st)
 {

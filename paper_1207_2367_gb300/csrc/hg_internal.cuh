@@ -27,8 +27,6 @@ struct DevScalars {
     int64_t tnext_bits;    // bit pattern of min_i tend_i (next-block pass 1, or the last correction)
     uint32_t arrive[4];    // CTAs done in next-block passes 1 and 2 and in the fused
                            // selection (the last one resets it); one spare
-    uint32_t bar_count;    // grid barrier of the fused block-step kernel: arrivals
-    uint32_t bar_gen;      //   and generation
 };
 
 enum : int32_t { ERR_TIMEOUT = 1, ERR_BADIDX = 2, ERR_STATE = 4, ERR_VALUE = 8, ERR_BOUNDS = 16 };

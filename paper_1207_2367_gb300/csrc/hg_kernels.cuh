@@ -18,26 +18,6 @@ struct StepParams {
 
 constexpr int64_t kNBChunk = 2048;   // particles per CTA in the next-block passes
 
-// Whole block steps of one system fused in one cooperative launch (hg_eval.cu):
-// selection and prediction, evaluation, j-split reduction and correction with
-// the next block time, separated by grid-wide barriers instead of kernel
-// boundaries; the same device code and launch plans as the separate kernels,
-// so the results are bitwise theirs.
-struct FusedArgs {
-    EvalArgs ev;       // records, list, partial sums, results (m and the plan are formed per step)
-    int32_t *idx;      // the active list (written by the selection)
-    State st;
-    int64_t n, npad;
-    DevScalars *sc;
-    PlanParams pq;
-    StepParams sp;
-    int steps;         // block steps per launch
-};
-// CTAs of the fused kernel when every one is resident (occupancy x SMs), 0 if
-// it cannot be launched cooperatively.
-int fused_grid(bool mixed, bool guard, int device, int num_sms);
-cudaError_t launch_fused_steps(bool mixed, const FusedArgs &fa, int grid, cudaStream_t s);
-
 int nb_grid(int64_t n);
 // part, cnt, off: nb_grid(n) entries each.
 cudaError_t launch_next_block(const State &st, int64_t n, double *part, int32_t *cnt, int32_t *off, int32_t *idx,

@@ -1,9 +1,8 @@
-// hg_step_dev.cuh -- device code of the block step shared by the separate
-// kernels (hg_kernels.cu) and the fused block-step kernel (hg_eval.cu): the
+// hg_step_dev.cuh -- device code of the block step (hg_kernels.cu): the
 // evaluation planner on one CTA, CTA reductions and arrival counts, the FP64
 // predictor (Sect. 3 item 1), the corrector with the Hermite interpolation and
 // the step criterion (Sect. 3 item 3, criterion equations, power-of-two
-// blocks).  Every translation unit that includes it gets its own copy.
+// blocks), and the passes of a graph-replayed block step.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -523,10 +522,9 @@ __device__ __forceinline__ void correct_lane(const State &st, const int32_t *idx
 
 // ------------------------------------------------------------------------
 // Passes of a graph-replayed block step of one system, taken by global thread
-// g of G (grid-stride): used by the separate kernels and by the fused
-// block-step kernel.  Data another CTA wrote in an earlier pass of the same
-// launch is read through L2 (__ldcg) or volatile, never from L1 or the
-// read-only path.
+// g of G (grid-stride).  State, lists and results are read through L2
+// (__ldcg) or volatile, never through the read-only path: a pass must see what
+// other CTAs wrote earlier, whatever kernel it runs in.
 // ------------------------------------------------------------------------
 
 // Table 1 sections 1-2 in one pass: predict every record to t_next (bit
@@ -589,44 +587,6 @@ __device__ void next_min_pass(const State &st, int64_t n, DevScalars *sc, long l
     }
     low = block_min_ll(low, sh);
     if (threadIdx.x == 0 && low != LLONG_MAX) atomicMin((long long *)&sc->tnext_bits, low);
-}
-
-// Grid-wide barrier of a cooperative launch (every CTA resident at once): each
-// CTA arrives on *count (release), the last one resets it and advances *gen
-// (release), the others wait for *gen to change (acquire; the wait is bounded
-// by kWaitCycles, after which ERR_TIMEOUT is set and false returned).  The
-// async proxy (bulk tile copies) is fenced on both sides.
-__device__ bool grid_sync(uint32_t *count, uint32_t *gen, int32_t *err)
-{
-    __shared__ int s_ok;
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t g0, old;
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g0) : "l"(gen) : "memory");
-        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
-        int ok = 1;
-        if (old == gridDim.x - 1) {
-            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(count) : "memory");
-            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(gen), "r"(g0 + 1u) : "memory");
-        } else {
-            const long long t0 = clock64();
-            for (;;) {
-                uint32_t gv;
-                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(gv) : "l"(gen) : "memory");
-                if (gv != g0) break;
-                if (clock64() - t0 > kWaitCycles) {
-                    atomicOr(err, ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-            }
-        }
-        s_ok = ok;
-    }
-    __syncthreads();
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-    return s_ok != 0;
 }
 
 }  // namespace

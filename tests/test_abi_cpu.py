@@ -33,7 +33,7 @@ def test_default_opts_without_gpu():
     o = binding.hg_default_opts()
     assert o.dt_min == 2.0 ** -25 and o.dt_max == 0.125 and o.eta_init == 0.01
     assert o.precision == binding.HG_FP64 and o.graph_steps == 8 and o.start_mode == 0 and o.profile == 0
-    assert o.test_stall_eval == 0 and o.order == 6 and o.fused_steps == 0
+    assert o.test_stall_eval == 0 and o.order == 6
 
 
 def test_struct_layouts_match_the_header(tmp_path):
