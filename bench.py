@@ -693,6 +693,7 @@ def run_interval(a, rank, world, dist):
     stream = torch.cuda.Stream()
     mixed = a.precision == "mixed"
     prec = hg.HG_MIXED if mixed else hg.HG_FP64
+    peaks = measure_peaks(hg, local, stream) if rank == 0 else None
     p = inputs.plummer(a.n, a.seed + rank, imf=a.imf)
     ctx = make_ctx(hg, p, a, prec, stream, local, profile=0)
     tuning = tune(hg, ctx, a)
@@ -778,7 +779,8 @@ def run_interval(a, rank, world, dist):
                          "inputs resident in HBM",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline(hg, prof_inter, prof, mixed, mhz, kind,
-                             EVAL_TRAFFIC.get((a.n, a.imf, a.precision, a.warmup, a.steps)) if a.block_steps == 0 else None),
+                             EVAL_TRAFFIC.get((a.n, a.imf, a.precision, a.warmup, a.steps)) if a.block_steps == 0 else None,
+                             peaks),
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,
