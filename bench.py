@@ -437,6 +437,10 @@ def run_headline(a, rank, world, dist):
         roof["pairs_per_launch"] = inter / max(1, steps_taken)
         e2e = run_e2e_blocks(a, hg, ctx, bs) if (not a.no_e2e and rank == 0) else None
         subset = subset_vs_fp64(hg, ctx, p, a, stream, local) if (not a.no_fp64 and rank == 0) else None
+        if subset and peaks and peaks.get("f64"):
+            subset["fp64_frac_of_measured_fp64_peak"] = subset["fp64_rate"] * FLOPS_F64 / 1e12 / peaks["f64"]
+            subset["mixed_frac_of_measured_fp32_peak"] = subset["mixed_rate"] * FLOPS_F32 / 1e12 / max(
+                peaks.get("f32", 0.0), peaks.get("f32x2", 0.0))
     finally:
         hg.hg_free(ctx)
     energy = energy_comparison(hg, stream, local) if (not a.no_fp64 and rank == 0) else None
