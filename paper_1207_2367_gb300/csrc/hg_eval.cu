@@ -437,8 +437,7 @@ constexpr size_t smem_bytes()
 }
 
 // The work items (i-tile, j-chunk) of one evaluation that this CTA takes
-// (items blockIdx.x, blockIdx.x + gridDim.x, ...): the body of k_eval and the
-// evaluation phase of the fused block-step kernel.  bars: the kStages
+// (items blockIdx.x, blockIdx.x + gridDim.x, ...): the body of k_eval.  bars: the kStages
 // initialised mbarriers of the tile ring; seq: tiles this CTA consumed so far
 // (their phase bookkeeping, carried across calls).  False when a bounded wait
 // expired (ERR_TIMEOUT is set; the copies in flight have been waited for).
@@ -609,7 +608,7 @@ __device__ __forceinline__ void put_result(const EvalArgs &a, double *ra, double
 }
 
 // The reduction's values taken by global thread g of G threads (grid-stride):
-// the body of k_reduce and the reduction phase of the fused block-step kernel.
+// the body of k_reduce.
 // Each (particle, value) sum has a fixed order whichever thread takes it.
 __device__ void reduce_values(const EvalArgs &args, int64_t m, const Plan &pl, double *ra, double *rj, double *rs,
                               int64_t g, int64_t G)
