@@ -16,8 +16,9 @@ summed exactly) and compare with the FP64 oracle:
     kappa.
 So per-particle 1e-6 is not a property any FP32 pair arithmetic has; the
 parity tests of the mixed path bound the normwise error and the error relative
-to the condition scale instead (plus the per-particle error of well-conditioned
-particles).
+to the condition scale instead, plus the per-particle error of particles with
+kappa <= 10 (99 % of a Plummer sphere's particles), where FP32 pair terms do
+meet it.
 """
 import numpy as np
 
@@ -85,5 +86,11 @@ def test_plummer_errors_follow_the_condition_number():
     # divided by kappa is a few float32 roundings at most, and the largest
     # per-particle errors belong to particles with kappa well above the median.
     assert (per / kappa).max() < 1e-6
+    # Up to kappa = 10 the per-particle tolerance itself holds, and such
+    # particles are nearly all of the sphere, its centre included.
+    assert per[kappa <= 10.0].max() < 1e-6
+    assert (kappa <= 10.0).mean() > 0.98
+    centre = np.argsort(np.linalg.norm(p.pos, axis=1))[: n // 20]
+    assert (kappa[centre] <= 10.0).mean() > 0.9
     worst = np.argsort(per)[-10:]
     assert np.median(kappa[worst]) > 3.0 * np.median(kappa)

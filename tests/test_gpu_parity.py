@@ -6,8 +6,11 @@ Mixed path (tolerances 1e-6 / 1e-5 / 1e-4 on acc / jerk / snap), all of:
   - normwise relative error of the output array, ||X - REF||_F / ||REF||_F;
   - per particle, the error relative to the condition scale sum_j ||term_ij||
     (oracle), i.e. relative to what any FP32 summation of the terms can resolve;
-  - per-particle relative error for every particle whose sum is well
-    conditioned (sum_j ||term_ij|| <= 2 ||ref_i||).
+  - per-particle relative error for every particle whose sum is not badly
+    conditioned (condition number kappa_i = sum_j ||term_ij|| / ||ref_i|| <= 10:
+    99 % of a Plummer sphere's particles, the dense centre included; FP32 pair
+    terms leave a per-particle error of up to ~1e-7 kappa_i, see
+    test_fp32_pair_limits.py).
 Integer and index work (block selection) is compared bit for bit.
 """
 import math
@@ -22,6 +25,7 @@ from gpu_util import DT_MAX, DT_MIN, gpu_context, gpu_eval, gpu_state, oracle_sy
 pytestmark = pytest.mark.gpu
 
 TOL = {0: (1e-12, 1e-12, 1e-12), 1: (1e-6, 1e-5, 1e-4)}
+KAPPA_PER_PARTICLE = 10.0   # mixed path: the per-particle tolerance binds up to this condition number
 
 
 def check_eval(got, ref, precision, absum=None):
@@ -37,9 +41,9 @@ def check_eval(got, ref, precision, absum=None):
             scale = absum[:, k]
             cond = np.linalg.norm(g - r, axis=1) / np.where(scale > 0, scale, 1.0)
             assert cond.max() <= tol, f"{name}: conditioned rel err {cond.max():.3e} > {tol:.0e}"
-            well = scale <= 2.0 * np.linalg.norm(r, axis=1)
+            well = scale <= KAPPA_PER_PARTICLE * np.linalg.norm(r, axis=1)
             if well.any():
-                assert per[well].max() <= tol, f"{name}: well-conditioned max rel err {per[well].max():.3e}"
+                assert per[well].max() <= tol, f"{name}: max rel err at kappa <= 10 {per[well].max():.3e}"
 
 
 # --------------------------------------------------------------------------
