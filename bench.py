@@ -40,6 +40,8 @@ import time
 
 import numpy as np
 
+PROCESS_T0 = time.perf_counter()   # the whole run's wall clock, reported beside the device-timed line
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -477,6 +479,7 @@ def run_headline(a, rank, world, dist):
         "peaks_measured_tflops": peaks,
         "tuning": tuning,
         "mixed_vs_fp64": {"subset_at_n": subset, "energy_job": energy},
+        "process_wall_s": time.perf_counter() - PROCESS_T0,
     }), flush=True)
 
 
