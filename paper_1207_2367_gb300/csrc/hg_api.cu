@@ -315,6 +315,18 @@ int enqueue_block_step(hg_ctx *c, cudaStream_t s, const cudaEvent_t *ev)
     return HG_OK;
 }
 
+// A bound state (hg_bind_device) may have been written by the caller since the
+// last call: rebuild what is derived from it (tend, the FP32 copies) before a
+// call reads it.
+int sync_bound(hg_ctx *c)
+{
+    if (!c->bound) return HG_OK;
+    HG_CUDA(c, launch_tend(c->st, c->n, c->stream));
+    c->kernels += 1;
+    c->tnext_valid = false;
+    return HG_OK;
+}
+
 // Graph steps of one system start from d_sc->tnext_bits: compute it when the
 // state changed by other means (start-up, hg_set_state, hg_correct).
 int ensure_tnext(hg_ctx *c)
@@ -462,6 +474,10 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
         if (c->npad > (int64_t)INT32_MAX) return fail(c, HG_EINVAL, "too many padded records");
     }
     bool ok = alloc_state(c, c->st) && alloc_state(c, c->st2);
+    if (c->mixed) {   // the FP32 copies read by the mixed predictor (4 float4 per particle)
+        c->st.f32 = dalloc<float4>(c, 4 * n);
+        ok = ok && c->st.f32;
+    }
     c->own = c->st;
     if (c->mixed) {
         for (int q = 0; q < kMixedArrays; ++q) {   // record pairs: six float4 arrays and one float2
@@ -571,10 +587,12 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
     for (int64_t i = 0; i < n; ++i) iota[(size_t)i] = (int32_t)i;
     HG_CUDA(c, cudaMemcpyAsync(c->d_idx, iota.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
     if (c->bv.nc > 0) HG_CUDA(c, launch_pad_records(c->mixed, c->rec, c->npad, c->stream));
+    HG_CUDA(c, launch_f32(c->st, n, c->stream));
     HG_CUDA(c, launch_predict(c->mixed, c->st, c->rec, n, c->npad, nullptr, 0.0, nullptr, rmap_of(c), c->stream));
     rc = run_eval_host_m(c, n);
     if (rc) return rc;
     HG_CUDA(c, launch_start(c->st, n, c->ra, c->rj, c->rs, step_params(c), c->stream));
+    HG_CUDA(c, launch_f32(c->st, n, c->stream));
     rc = sync_scalars(c);
     if (rc) return rc;
     invalidate(c);
@@ -842,6 +860,7 @@ int hg_next_block(hg_ctx *c, double *t_next, int32_t *idx, int64_t cap, int64_t 
 {
     const CallRange range_("hg_next_block");
     if (!c) return HG_EINVAL;
+    if (const int rb = sync_bound(c)) return rb;
     HG_CUDA(c, launch_next_block(c->st, c->n, c->nb_part, c->nb_cnt, c->nb_off, c->d_idx, c->d_sc, 0, c->pp,
                                  c->stream));
     c->kernels += 3;
@@ -865,6 +884,7 @@ int hg_predict(hg_ctx *c, double t)
     const CallRange range_("hg_predict");
     if (!c) return HG_EINVAL;
     if (!isfinite(t)) return fail(c, HG_EINVAL, "t must be finite");
+    if (const int rb = sync_bound(c)) return rb;
     HG_CUDA(c, launch_predict(c->mixed, c->st, c->rec, c->n, c->npad, nullptr, t, nullptr, rmap_of(c), c->stream));
     c->kernels += 1;
     c->t_pred = t;
@@ -967,7 +987,8 @@ int hg_step(hg_ctx *c, int64_t n_steps)
     if (!c) return HG_EINVAL;
     if (n_steps < 0) return fail(c, HG_EINVAL, "n_steps must be >= 0");
     if (n_steps == 0) return HG_OK;
-    int rc = ensure_graphs(c);
+    int rc = sync_bound(c);
+    if (rc == HG_OK) rc = ensure_graphs(c);
     if (rc == HG_OK) rc = ensure_tnext(c);
     if (rc) return rc;
     invalidate(c);
@@ -984,7 +1005,8 @@ int hg_advance(hg_ctx *c, double t_end, int64_t *steps_out)
     const CallRange range_("hg_advance");
     if (!c) return HG_EINVAL;
     if (!isfinite(t_end)) return fail(c, HG_EINVAL, "t_end must be finite");
-    int rc = ensure_graphs(c);
+    int rc = sync_bound(c);
+    if (rc == HG_OK) rc = ensure_graphs(c);
     if (rc == HG_OK) rc = ensure_tnext(c);
     if (rc) return rc;
     invalidate(c);

@@ -33,9 +33,17 @@ enum : int32_t { ERR_TIMEOUT = 1, ERR_BADIDX = 2, ERR_STATE = 4, ERR_VALUE = 8, 
 
 // FP64 state of every particle at its own time, structure of arrays.
 // tend = t + dt (exact: dyadic) is kept beside t and dt for the block selection.
+// f32 (mixed contexts; nullptr otherwise): the FP32 roundings (d2f) of the
+// fields the mixed predictor takes in FP32, four float4 per particle:
+//   (v_x, v_y, v_z, m) (a_x, a_y, a_z, j_x) (j_y, j_z, s_x, s_y) (s_z, c_x, c_y, c_z)
+// kept equal to d2f of the FP64 fields by every kernel that writes them, and
+// rebuilt whenever the state is replaced from outside.
 struct State {
     double *mass, *x, *v, *a, *j, *s, *c, *t, *dt, *tend;
+    float4 *f32;
 };
+// Position of component k of each field in a particle's 16 FP32 values.
+constexpr int kF32V = 0, kF32M = 3, kF32A = 4, kF32J = 7, kF32S = 10, kF32C = 13;
 
 // ---------------------------------------------------------------------------
 // Predicted j-records ("j-data"), npad entries (npad a multiple of the j-tile).

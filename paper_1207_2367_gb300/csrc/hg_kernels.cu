@@ -285,13 +285,11 @@ __global__ void __launch_bounds__(128) k_correct(State st, const int32_t *idx, c
     __shared__ long long sh[32];
     const int64_t m = m_dev ? *m_dev : m_host;
     if (m <= 0) return;
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, G = (int64_t)gridDim.x * blockDim.x;
     long long low = LLONG_MAX;
-    correct_pass(st, idx, m, n, ra, rj, rs, rn, sp, &sc->err, ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
-                 ((int64_t)gridDim.x * blockDim.x) >> 5, low);
-    if (!min_pass) return;
-    const long long tb = __double_as_longlong(*((volatile double *)&sc->t_cur));
-    next_min_pass(st, n, sc, tb, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
-                  low, sh);
+    if (min_pass) low = scan_min_pass(st, n, __double_as_longlong(*((volatile double *)&sc->t_cur)), g, G);
+    correct_pass(st, idx, m, n, ra, rj, rs, rn, sp, &sc->err, g >> 5, G >> 5, low);
+    if (min_pass) publish_min(sc, low, sh);
 }
 
 
@@ -713,10 +711,19 @@ __global__ void k_pad_records(Records rec, int64_t npad)
 }
 
 // tend = t + dt for every particle (after the state is replaced).
+// The fields derived from the state: tend = t + dt and (mixed) the FP32 copies.
 __global__ void k_tend(State st, int64_t n)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         st.tend[i] = st.t[i] + st.dt[i];
+        if (st.f32) store_f32(st, i);
+    }
+}
+
+__global__ void k_f32(State st, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        store_f32(st, i);
 }
 
 inline int grid_for(int64_t work, int threads, int cap)
@@ -754,6 +761,13 @@ cudaError_t launch_next_min(const State &st, int64_t n, double *part, DevScalars
 cudaError_t launch_tend(const State &st, int64_t n, cudaStream_t s)
 {
     k_tend<<<grid_for(n, 256, 4096), 256, 0, s>>>(st, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f32(const State &st, int64_t n, cudaStream_t s)
+{
+    if (!st.f32) return cudaSuccess;
+    k_f32<<<grid_for(n, 256, 4096), 256, 0, s>>>(st, n);
     return cudaGetLastError();
 }
 

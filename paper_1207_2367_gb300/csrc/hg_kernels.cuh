@@ -31,8 +31,10 @@ cudaError_t launch_next_min(const State &st, int64_t n, double *part, DevScalars
 cudaError_t launch_predict_select(bool mixed, const State &st, const Records &rec, int64_t n, int64_t npad,
                                   int32_t *idx, DevScalars *sc, int count_step, const PlanParams &pq, int max_grid,
                                   cudaStream_t s);
-// tend = t + dt after the state was replaced.
+// After the state was replaced: tend = t + dt and the FP32 copies (st.f32).
 cudaError_t launch_tend(const State &st, int64_t n, cudaStream_t s);
+// The FP32 copies alone (a no-op for FP64 contexts, st.f32 == nullptr).
+cudaError_t launch_f32(const State &st, int64_t n, cudaStream_t s);
 // rmap: record of each particle (clusters), or nullptr (record i = particle i).
 cudaError_t launch_predict(bool mixed, const State &st, const Records &rec, int64_t n, int64_t npad,
                            const double *t_dev, double t_host, const int64_t *m_dev, const int32_t *rmap,

@@ -128,6 +128,24 @@ __device__ __forceinline__ Pred predict_one(const State &st, int64_t i, double t
     return p;
 }
 
+// The 16 FP32 values of particle i (mixed contexts), from its FP64 fields.
+__device__ __forceinline__ void store_f32(const State &st, int64_t i)
+{
+    float f[16];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int64_t q = 3 * i + k;
+        f[kF32V + k] = d2f(__ldcg(st.v + q));
+        f[kF32A + k] = d2f(__ldcg(st.a + q));
+        f[kF32J + k] = d2f(__ldcg(st.j + q));
+        f[kF32S + k] = d2f(__ldcg(st.s + q));
+        f[kF32C + k] = d2f(__ldcg(st.c + q));
+    }
+    f[kF32M] = d2f(__ldcg(st.mass + i));
+#pragma unroll
+    for (int w = 0; w < 4; ++w) st.f32[4 * i + w] = make_float4(f[4 * w], f[4 * w + 1], f[4 * w + 2], f[4 * w + 3]);
+}
+
 // Record r from particle i predicted to time tt (i >= n: a padding record).
 template <bool MIXED>
 __device__ __forceinline__ void predict_record(const State &st, const Records &rec, int64_t i, int64_t n, int64_t r,
@@ -145,15 +163,26 @@ __device__ __forceinline__ void predict_record(const State &st, const Records &r
                 // component, the FP64 pipe being this kernel's limit on GB300.
                 // Velocities and accelerations feed only the FP32 pair
                 // arithmetic: FP32 Horner series from the rounded derivatives.
+                // The FP32 inputs come rounded already (st.f32): the same
+                // values as d2f of the FP64 fields, without the conversions.
                 const double h = tt - __ldcg(st.t + i);
                 const float hf = d2f(h);
+                float f[16];
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const float4 u = __ldcg(st.f32 + 4 * i + w);
+                    f[4 * w] = u.x;
+                    f[4 * w + 1] = u.y;
+                    f[4 * w + 2] = u.z;
+                    f[4 * w + 3] = u.w;
+                }
                 float hi[3], lo[3], vp[3], ap[3];
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const int64_t q = 3 * i + k;
-                    const double x = __ldcg(st.x + q), v = __ldcg(st.v + q), a = __ldcg(st.a + q),
-                                 j = __ldcg(st.j + q), s = __ldcg(st.s + q), c = __ldcg(st.c + q);
-                    const float vf = d2f(v), af = d2f(a), jf = d2f(j), sf = d2f(s), cf = d2f(c);
+                    const double x = __ldcg(st.x + q), v = __ldcg(st.v + q);
+                    const float vf = f[kF32V + k], af = f[kF32A + k], jf = f[kF32J + k], sf = f[kF32S + k],
+                                cf = f[kF32C + k];
                     const float rest =
                         hf * hf *
                         fmaf(hf, fmaf(hf, fmaf(hf, cf * (1.f / 120.f), sf * (1.f / 24.f)), jf * (1.f / 6.f)), af * 0.5f);
@@ -164,7 +193,7 @@ __device__ __forceinline__ void predict_record(const State &st, const Records &r
                                  vf);
                     ap[k] = fmaf(hf, fmaf(hf, fmaf(hf, cf * (1.f / 6.f), sf * 0.5f), jf), af);
                 }
-                v = MixedRecord{hi[0], hi[1], hi[2], d2f(__ldcg(st.mass + i)), lo[0], lo[1], lo[2], ap[0],
+                v = MixedRecord{hi[0], hi[1], hi[2], f[kF32M], lo[0], lo[1], lo[2], ap[0],
                                 vp[0], vp[1], vp[2], ap[1], ap[2]};
             } else {
                 const float far = (float)kPadCoord;
@@ -263,9 +292,15 @@ __device__ __forceinline__ bool pow2_exponent(double h, int &k)
 // degree-5 interpolant through a, jerk, snap at both ends of the step.
 // h = 2^e: h/2, h^2/10 = 2^(2e) fl(1/10), h^3/120 = 2^(3e) fl(1/120) and the
 // reciprocal powers are exact scalings, equal to the divisions they replace.
+// Component k of one particle's fields at the start of its step, loaded in one
+// round trip with its t and dt.
+struct CorrIn {
+    double x0, v0, a0, j0, s0;
+};
+
 __device__ __forceinline__ void correct_component(const State &st, int64_t i, int k, double h, int e, bool pow2,
-                                                  double a1, double j1, double s1, double &c3, double &c4, double &c5,
-                                                  double &Ak)
+                                                  const CorrIn &in, double a1, double j1, double s1, double &c3,
+                                                  double &c4, double &c5, double &Ak)
 {
     double hh, h2, h3, ih3, ih4, ih5;
     if (pow2) {
@@ -285,8 +320,7 @@ __device__ __forceinline__ void correct_component(const State &st, int64_t i, in
         ih5 = ih4 * ih;
     }
     const int64_t q = 3 * i + k;
-    const double x0 = __ldcg(st.x + q), v0 = __ldcg(st.v + q), a0 = __ldcg(st.a + q), j0 = __ldcg(st.j + q),
-                 s0 = __ldcg(st.s + q);
+    const double x0 = in.x0, v0 = in.v0, a0 = in.a0, j0 = in.j0, s0 = in.s0;
     const double v1 = v0 + hh * (a1 + a0) - h2 * (j1 - j0) + h3 * (s1 + s0);
     const double x1 = x0 + hh * (v1 + v0) - h2 * (a1 - a0) + h3 * (j1 + j0);
     const double A = a1 - a0 - j0 * h - s0 * h * h / 2.0;
@@ -302,6 +336,14 @@ __device__ __forceinline__ void correct_component(const State &st, int64_t i, in
     st.j[q] = j1;
     st.s[q] = s1;
     st.c[q] = c3;
+    if (st.f32) {
+        float *f = reinterpret_cast<float *>(st.f32 + 4 * i);
+        f[kF32V + k] = d2f(v1);
+        f[kF32A + k] = d2f(a1);
+        f[kF32J + k] = d2f(j1);
+        f[kF32S + k] = d2f(s1);
+        f[kF32C + k] = d2f(c3);
+    }
 }
 
 // 4th-order scheme, component k of particle i (the two-point Hermite corrector
@@ -310,7 +352,8 @@ __device__ __forceinline__ void correct_component(const State &st, int64_t i, in
 // and snap and crackle at the step's end for the p = 4 criterion.  h = 2^e:
 // h^2/12 = 2^(2e) fl(1/12) and the reciprocal powers are exact scalings.
 __device__ __forceinline__ void correct4_component(const State &st, int64_t i, int k, double h, int e, bool pow2,
-                                                   double a1, double j1, double &s1, double &c1, double &Ak)
+                                                   const CorrIn &in, double a1, double j1, double &s1, double &c1,
+                                                   double &Ak)
 {
     double hh, h2, ih2, ih3;
     if (pow2) {
@@ -325,7 +368,7 @@ __device__ __forceinline__ void correct4_component(const State &st, int64_t i, i
         ih3 = ih2 / h;
     }
     const int64_t q = 3 * i + k;
-    const double x0 = __ldcg(st.x + q), v0 = __ldcg(st.v + q), a0 = __ldcg(st.a + q), j0 = __ldcg(st.j + q);
+    const double x0 = in.x0, v0 = in.v0, a0 = in.a0, j0 = in.j0;
     const double v1 = v0 + hh * (a0 + a1) + h2 * (j0 - j1);
     const double x1 = x0 + hh * (v0 + v1) + h2 * (a0 - a1);
     const double c = (12.0 * (a0 - a1) + 6.0 * h * (j0 + j1)) * ih3;
@@ -339,6 +382,14 @@ __device__ __forceinline__ void correct4_component(const State &st, int64_t i, i
     st.j[q] = j1;
     st.s[q] = 0.0;
     st.c[q] = 0.0;
+    if (st.f32) {
+        float *f = reinterpret_cast<float *>(st.f32 + 4 * i);
+        f[kF32V + k] = d2f(v1);
+        f[kF32A + k] = d2f(a1);
+        f[kF32J + k] = d2f(j1);
+        f[kF32S + k] = 0.f;
+        f[kF32C + k] = 0.f;
+    }
 }
 
 // ---- FP32 estimate of floor(log2 crit) for the step criterion --------------
@@ -425,18 +476,18 @@ __device__ __forceinline__ bool multiple_of_pow2(double t1, int p)
 
 __device__ __forceinline__ double sq3(const double *p) { return p[0] * p[0] + p[1] * p[1] + p[2] * p[2]; }
 
-// New time and p = 6 step of particle i from d = a^(0..5) at the step's end.
+// New time t0 + h and p = 6 step of particle i from d = a^(0..5) at the step's end.
 // A: the acceleration change left after a0 + j0 h + s0 h^2/2 (a0 + j0 h for
 // p = 4).  Below the noise floor of the evaluation, sp.noise_rel times the
 // noise scale (sum_j m_j / r_ij^2 where the evaluation provides it, else |a1|;
 // compared as squares), the interpolated derivatives are noise and the
 // criterion may not shrink the step.
 template <int P>
-__device__ __forceinline__ double finish_step(const State &st, int64_t i, double h, int e, bool pow2,
+__device__ __forceinline__ double finish_step(const State &st, int64_t i, double t0, double h, int e, bool pow2,
                                               const double (*d)[3], const double *A, double scale2,
                                               const StepParams &sp, bool store)
 {
-    const double t1 = __ldcg(st.t + i) + h;
+    const double t1 = t0 + h;
     const bool noisy = sp.noise_rel > 0.0 && sq3(A) < (sp.noise_rel * sp.noise_rel) * scale2;
     double dt1;
     int F, kmin, kmax;
@@ -485,24 +536,39 @@ __device__ __forceinline__ void correct_lane(const State &st, const int32_t *idx
     const int lane = threadIdx.x & 31, sub = lane / 3, k = lane - 3 * sub;
     const int64_t q = u * kCorrUnit + sub;
     bool act = sub < kCorrUnit && q < m;
-    const int32_t iq = act ? __ldcg(idx + q) : 0;
+    // What is indexed by the list position q is loaded at once, then the
+    // particle's own fields in one more round trip: the chain of dependent
+    // loads ahead of the arithmetic is two deep.
+    int32_t iq = 0;
+    double dk[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, rnq = 0.0;
+    if (act) {
+        iq = __ldcg(idx + q);
+        dk[0] = __ldcg(ra + 3 * q + k);
+        dk[1] = __ldcg(rj + 3 * q + k);
+        if (P == 6) dk[2] = __ldcg(rs + 3 * q + k);
+        if (rn) rnq = __ldcg(rn + q);
+    }
     if (act && !in_bounds(iq >= 0 && (int64_t)iq < n, err)) act = false;
-    double dk[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, Ak = 0.0, h = 1.0;
+    double Ak = 0.0, h = 1.0, t0 = 0.0;
     int64_t i = 0;
     int e = 0;
     bool pow2 = false;
     if (act) {
         i = iq;
+        const int64_t qk = 3 * i + k;
         h = __ldcg(st.dt + i);
+        t0 = __ldcg(st.t + i);
+        CorrIn in;
+        in.x0 = __ldcg(st.x + qk);
+        in.v0 = __ldcg(st.v + qk);
+        in.a0 = __ldcg(st.a + qk);
+        in.j0 = __ldcg(st.j + qk);
+        in.s0 = P == 6 ? __ldcg(st.s + qk) : 0.0;
         pow2 = pow2_exponent(h, e);
-        dk[0] = __ldcg(ra + 3 * q + k);
-        dk[1] = __ldcg(rj + 3 * q + k);
-        if (P == 4) {
-            correct4_component(st, i, k, h, e, pow2, dk[0], dk[1], dk[2], dk[3], Ak);
-        } else {
-            dk[2] = __ldcg(rs + 3 * q + k);
-            correct_component(st, i, k, h, e, pow2, dk[0], dk[1], dk[2], dk[3], dk[4], dk[5], Ak);
-        }
+        if (P == 4)
+            correct4_component(st, i, k, h, e, pow2, in, dk[0], dk[1], dk[2], dk[3], Ak);
+        else
+            correct_component(st, i, k, h, e, pow2, in, dk[0], dk[1], dk[2], dk[3], dk[4], dk[5], Ak);
     }
     double d[6][3], A[3];
     const int base = 3 * sub;
@@ -514,8 +580,8 @@ __device__ __forceinline__ void correct_lane(const State &st, const int32_t *idx
         A[c] = __shfl_sync(0xffffffffu, Ak, src);
     }
     if (act) {
-        const double scale2 = rn ? __ldcg(rn + q) * __ldcg(rn + q) : sq3(d[0]);
-        low = min(low, __double_as_longlong(finish_step<P>(st, i, h, e, pow2, d, A, scale2, sp, k == 0)));
+        const double scale2 = rn ? rnq * rnq : sq3(d[0]);
+        low = min(low, __double_as_longlong(finish_step<P>(st, i, t0, h, e, pow2, d, A, scale2, sp, k == 0)));
     }
 }
 
@@ -573,18 +639,25 @@ __device__ void correct_pass(const State &st, const int32_t *idx, int64_t m, int
 }
 
 // Next block time: the minimum over the new tend of the corrected particles
-// (low, from correct_pass) and over every particle whose tend differs from the
-// block time tb; one atomicMin per CTA into sc->tnext_bits.  A particle of the
-// block read while another CTA corrects it shows either its old tend (== tb:
-// skipped, its new value is in that CTA's minimum) or its new one (final).
-__device__ void next_min_pass(const State &st, int64_t n, DevScalars *sc, long long tb, int64_t g, int64_t G,
-                              long long low, long long *sh)
+// (from correct_pass) and over every particle whose tend differs from the
+// block time tb (this pass, taken before the correction so that its loads
+// overlap the corrector's): a particle of the block read while some CTA
+// corrects it shows either its old tend (== tb: skipped, its new value is in
+// that CTA's minimum) or its new one (final).
+__device__ long long scan_min_pass(const State &st, int64_t n, long long tb, int64_t g, int64_t G)
 {
     const volatile long long *bits = reinterpret_cast<const volatile long long *>(st.tend);
+    long long low = LLONG_MAX;
     for (int64_t i = g; i < n; i += G) {
         const long long v = bits[i];
         if (v != tb) low = min(low, v);
     }
+    return low;
+}
+
+// One atomicMin per CTA of its threads' minima into sc->tnext_bits.
+__device__ void publish_min(DevScalars *sc, long long low, long long *sh)
+{
     low = block_min_ll(low, sh);
     if (threadIdx.x == 0 && low != LLONG_MAX) atomicMin((long long *)&sc->tnext_bits, low);
 }

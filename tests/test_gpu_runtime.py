@@ -243,6 +243,54 @@ def test_bind_device_state_lives_in_caller_tensors(hg):
             hg.hg_free(ctx)
 
 
+def test_bound_mixed_state_written_in_place(hg):
+    """A mixed context bound to caller tensors whose velocities, accelerations
+    and time steps the caller changes in place between calls: the next block
+    steps take the new values (the FP32 copies the mixed predictor reads and the
+    step ends are rebuilt from the bound arrays), bitwise like an unbound
+    context handed the same state through hg_set_state."""
+    import torch
+    n, eps = 2000, 1e-3
+    p = inputs.plummer(n, 43)
+    o = hg.hg_default_opts(precision=hg.HG_MIXED, dt_max=DT_MAX)
+    a = hg.hg_init(p.mass, p.pos, p.vel, eps, 0.45, o)
+    b = hg.hg_init(p.mass, p.pos, p.vel, eps, 0.45, o)
+    try:
+        bufs = hg.new_state(n, like="cuda")
+        hg.hg_bind_device(a, bufs, copy_in=True)
+        hg.hg_step(a, 12)
+        hg.hg_step(b, 12)
+        torch.cuda.synchronize()
+        ref, t_ref = gpu_state(hg, b, n)
+        for f in hg.STATE_FIELDS:
+            np.testing.assert_array_equal(bufs[f].cpu().numpy(), ref[f], err_msg=f)
+        # The caller's edits, in place on the device and the same on the host copy.
+        bufs["vel"].mul_(1.001)
+        bufs["acc"].mul_(0.999)
+        bufs["crackle"].mul_(1.5)
+        ref["vel"] = ref["vel"] * 1.001
+        ref["acc"] = ref["acc"] * 0.999
+        ref["crackle"] = ref["crackle"] * 1.5
+        # halve the step of the particles whose step ends last (still a power of
+        # two with t a multiple of it)
+        dt = bufs["dt"]
+        sel = (dt == dt.max()) & (dt > DT_MIN)
+        dt[sel] *= 0.5
+        ref["dt"] = dt.cpu().numpy().copy()
+        torch.cuda.synchronize()
+        hg.hg_set_state(b, ref, t_ref)
+        for ctx in (a, b):
+            hg.hg_step(ctx, 12)
+        torch.cuda.synchronize()
+        got, _ = gpu_state(hg, b, n)
+        for f in hg.STATE_FIELDS:
+            np.testing.assert_array_equal(bufs[f].cpu().numpy(), got[f], err_msg=f)
+        assert hg.hg_get_stats(a)["t_sys"] == hg.hg_get_stats(b)["t_sys"]
+    finally:
+        for ctx in (a, b):
+            hg.hg_free(ctx)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_identical_contexts_stay_bitwise_identical(hg, precision):
     """Determinism: two contexts with the same input take 200 graph-replayed
