@@ -182,7 +182,7 @@ struct Mixed {
             selfp[k] = (r / TJ == tile) ? (int)((r % TJ) >> 1) : -1;
             selfk[k] = (r & 1) ? f2_pack(1.f, 0.f) : f2_pack(0.f, 1.f);
         }
-        const int ppt = TP / tpi;   // pairs per lane in this tile
+        const int ppt = TP >> (__ffs(tpi) - 1);   // pairs per lane in this tile (tpi a power of two)
         const int fold = ppt < kFold / 2 ? ppt : kFold / 2;
         for (int g = 0; g < ppt; g += fold) {
             f2_t ch[I][9], cn[I];
@@ -374,7 +374,7 @@ struct F64 {
                                 Eps eps2, int64_t)
     {
         const double2 *q0 = reinterpret_cast<const double2 *>(sb);
-        const int jpt = TJ / tpi;
+        const int jpt = TJ >> (__ffs(tpi) - 1);   // tpi a power of two
 #pragma unroll 2
         for (int u = 0; u < jpt; ++u) {
             const int jj = u * tpi + lane_j;
@@ -491,7 +491,7 @@ __device__ bool eval_items(const EvalArgs &args, int64_t m, const Plan &pl, unsi
         if (!in_bounds(tbase >= 0 && nt64 >= 0 && tbase + nt64 <= args.npad / P::TJ, args.err)) nt64 = 0;
         const int nt = (int)nt64;
         const int lane_j = tid & (tpi - 1);
-        const int slot = tid / tpi;
+        const int slot = tid >> (__ffs(tpi) - 1);   // tid / tpi (a power of two)
 
         typename P::ITile iv;
         int64_t qi[P::I];
@@ -647,9 +647,12 @@ __device__ void reduce_values(const EvalArgs &args, int64_t m, const Plan &pl, d
     } else {
         // Many chunks (small blocks): one warp per (particle, value); lane l
         // sums chunks l, l+32, ..., then a fixed butterfly combines the lanes.
-        const int lane = (int)(g & 31);
-        const int64_t wid = g >> 5;
-        const int64_t nw = G >> 5;
+        // Consecutive (particle, value) pairs go to warps of different CTAs, so
+        // that a small block's few sums run on as many FP64 units (one per
+        // scheduler, ~64 cycles per warp instruction) as there are sums.
+        const int lane = (int)(threadIdx.x & 31);
+        const int64_t wid = (int64_t)blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5);
+        const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
         for (int64_t e = wid; e < total; e += nw) {
             const int64_t q = e / kOut;
             const int c = (int)(e - q * kOut);

@@ -4,7 +4,9 @@
 
 Builds a Plummer sphere (Henon units), creates a context (the start-up
 evaluation has every particle active), replays --steps block steps from CUDA
-graphs and prints the device counters.  Used for profiling single kernels.
+graphs and prints the device counters; --eval-m then times evaluations (evaluation
+and j-split reduction kernels) of that many particles.  Used for profiling single
+kernels.
 """
 from __future__ import annotations
 
@@ -23,6 +25,9 @@ def main(argv=None):
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--steps", type=int, default=0)
     ap.add_argument("--dt-max", type=float, default=1.0 / 16)
+    ap.add_argument("--eval-m", type=int, default=0,
+                    help="then time evaluations of m particles spread over the system (hg_time_evaluate)")
+    ap.add_argument("--eval-reps", type=int, default=20)
     a = ap.parse_args(argv)
 
     from . import binding as hg
@@ -40,6 +45,12 @@ def main(argv=None):
             hg.hg_step(ctx, a.steps)
         stats = hg.hg_get_stats(ctx)
         stats.update(n=a.n, init_s=t_init, steps_s=time.perf_counter() - t0)
+        if a.eval_m:
+            import numpy as np
+            lst = np.unique(np.linspace(0, a.n - 1, a.eval_m).astype(np.int32))
+            hg.hg_predict(ctx, stats["t_sys"])
+            stats.update(eval_m=int(lst.shape[0]),
+                         eval_us=hg.hg_time_evaluate(ctx, lst, lst.shape[0], a.eval_reps))
         print(json.dumps(stats))
     finally:
         hg.hg_free(ctx)
