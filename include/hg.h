@@ -113,6 +113,12 @@ void hg_default_opts(hg_opts *opts);
  * crackle = 0, first steps from the p = 4 criterion with opts->eta_init,
  * quantized to powers of two in [dt_min, dt_max].  opts may be NULL.
  * With eps = 0 particles at the same position exert no force on each other.
+ * Value limits (HG_EINVAL beyond them), the ranges the pair arithmetic keeps
+ * finite in: mixed |positions| <= 1e15, |velocities| <= 1e30, FP64 both 1e150;
+ * eps at most the position limit; every mass <= L min(1, eps^3) with L = 1e37
+ * (mixed) or 1e300 (FP64), only <= L with eps = 0, so that m / (r^2 + eps^2)
+ * and m / (r^2 + eps^2)^(3/2) stay finite for every pair.  hg_set_state and hg_bind_device check the same limits (and
+ * 1e30 / 1e150 for the higher derivatives).
  * Errors: HG_EINVAL, HG_ENOMEM, HG_ECUDA. */
 int hg_init(hg_ctx **out, int64_t n, const double *mass, const double *pos, const double *vel,
             double eps, double eta, const hg_opts *opts);
@@ -240,7 +246,9 @@ const char *hg_init_error(void);
  * data directly.
  *   n          particles, 1 <= n <= 16384 (larger n: HG_EINVAL);
  *   mass       [n], pos, vel, acc_pred [n][3]: predicted masses, positions,
- *              velocities and accelerations, FP64, device memory;
+ *              velocities and accelerations, FP64, device memory, within the
+ *              limits hg_init checks (not checked here: values beyond them give
+ *              non-finite results);
  *   eps        softening >= 0; precision HG_FP64 or HG_MIXED;
  *   idx        [m] device int32, strictly increasing, in [0, n) (HG_EINVAL otherwise);
  *   acc, jerk, snap  [m][3] FP64 device outputs; stream  cudaStream_t or NULL.

@@ -205,7 +205,7 @@ EvalArgs eval_args(hg_ctx *c, const int64_t *m_dev, int64_t m_host)
     a.plan_host = m_dev ? Plan{} : make_plan(m_host, c->pp);
     a.partial = c->partial;
     a.eps2 = c->eps * c->eps;
-    a.guard = c->eps == 0.0 ? 1 : 0;
+    a.guard = c->eps * c->eps < kGuardEps2 ? 1 : 0;
     a.tx_extra = c->opts.test_stall_eval ? 16u : 0u;
     a.err = &c->d_sc->err;
     a.bv = c->bv;
@@ -560,15 +560,16 @@ int init_impl(hg_ctx *c, const double *mass, const double *pos, const double *ve
     int rc = device_check(
         c,
         [&](int32_t *f) {
-            return launch_validate_init(c->st.mass, c->st.x, c->st.v, n, value_limits(c->mixed), f, c->stream);
+            return launch_validate_init(c->st.mass, c->st.x, c->st.v, n, value_limits(c->mixed, c->eps), f, c->stream);
         },
         &flag);
     if (rc) return rc;
     if (flag)
         return fail(c, HG_EINVAL,
-                    c->mixed ? "masses must be finite and > 0, |positions| <= 1e15 and |velocities| <= 1e30 (the "
-                               "FP32 range of the mixed pair arithmetic)"
-                             : "masses must be finite and > 0, |positions| and |velocities| <= 1e150");
+                    c->mixed ? "masses must be finite, > 0 and <= 1e37 min(1, eps^3), |positions| <= 1e15 and "
+                               "|velocities| <= 1e30 (the FP32 range of the mixed pair arithmetic)"
+                             : "masses must be finite, > 0 and <= 1e300 min(1, eps^3), |positions| and |velocities| "
+                               "<= 1e150");
 
     // Start-up: every particle active at t = 0; the prediction is the identity.
     for (double *p : {c->st.a, c->st.j, c->st.s, c->st.c})
@@ -821,6 +822,8 @@ int hg_init_batch(hg_ctx **out, int32_t n_clusters, const int64_t *offsets, int6
     else
         hg_default_opts(&o);
     if (o.precision != HG_FP64 && o.precision != HG_MIXED) return bad("precision must be HG_FP64 or HG_MIXED");
+    if (eps > value_limits(o.precision == HG_MIXED, eps).pos)
+        return bad("eps must not exceed the position limit (mixed 1e15, FP64 1e150)");
     if (o.energy_precision != HG_FP64 && o.energy_precision != HG_MIXED) return bad("bad energy_precision");
     if (!is_pow2(o.dt_min) || !is_pow2(o.dt_max) || o.dt_min > o.dt_max)
         return bad("dt_min and dt_max must be powers of two with dt_min <= dt_max");
@@ -1134,16 +1137,16 @@ int hg_set_state(hg_ctx *c, const hg_state *in)
     int rc = device_check(
         c,
         [&](int32_t *fl) {
-            return launch_validate_state(c->st2, n, c->opts.dt_min, c->opts.dt_max, value_limits(c->mixed), fl,
+            return launch_validate_state(c->st2, n, c->opts.dt_min, c->opts.dt_max, value_limits(c->mixed, c->eps), fl,
                                          c->stream);
         },
         &flag);
     if (rc) return rc;
     if (flag)
         return fail(c, HG_EINVAL,
-                    "state check failed: masses > 0, finite values within the limits (mixed: |positions| <= "
-                    "1e15, other fields <= 1e30; FP64: 1e150), dt a power of two in [dt_min, dt_max], t a "
-                    "multiple of dt");
+                    "state check failed: masses > 0 and <= L min(1, eps^3), finite values within the limits "
+                    "(mixed: L = 1e37, |positions| <= 1e15, other fields <= 1e30; FP64: L = 1e300, 1e150), dt a "
+                    "power of two in [dt_min, dt_max], t a multiple of dt");
     // Copy into the live arrays (captured graphs keep their pointers).
     const State &d = c->st, &s = c->st2;
     struct G {
@@ -1207,7 +1210,7 @@ int hg_bind_device(hg_ctx *c, const hg_state *dev, int copy_in)
             rc = device_check(
                 c,
                 [&](int32_t *fl) {
-                    return launch_validate_state(b, n, c->opts.dt_min, c->opts.dt_max, value_limits(c->mixed), fl,
+                    return launch_validate_state(b, n, c->opts.dt_min, c->opts.dt_max, value_limits(c->mixed, c->eps), fl,
                                                  c->stream);
                 },
                 &flag);

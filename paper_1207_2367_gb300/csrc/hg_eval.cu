@@ -22,6 +22,10 @@ namespace hg {
 namespace {
 
 constexpr int kFold = 32;   // FP32 pair sums are folded into the compensated sum every kFold j's
+// Smallest normal float.  With eps^2 below 2^-100 (the guarded evaluation) the
+// softened r^2 of a particle with itself is zero or subnormal in FP32, where the
+// flush-to-zero reciprocal square root gives infinity: such pairs are skipped.
+constexpr float kFltMinNormal = 1.17549435e-38f;
 
 // ------------------------------------------------------------------------
 // Mixed precision: FP32 pair arithmetic, double-single position differences,
@@ -122,9 +126,9 @@ struct Mixed {
         const f2_t r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_fma(dx, dx, eps2)));
         const float2 r2s = f2_unpack(r2);
         float y0 = rsqrt_approx(r2s.x), y1 = rsqrt_approx(r2s.y);
-        if (GUARD) {
-            y0 = r2s.x > 0.f ? y0 : 0.f;
-            y1 = r2s.y > 0.f ? y1 : 0.f;
+        if (GUARD) {   // r^2 below FP32's normal range: a pair at zero distance, skipped
+            y0 = r2s.x >= kFltMinNormal ? y0 : 0.f;
+            y1 = r2s.y >= kFltMinNormal ? y1 : 0.f;
         }
         // The hardware reciprocal square root is used as it is: a Newton-Raphson
         // step in FP32 cannot improve on its ~1-ulp result, and measured against

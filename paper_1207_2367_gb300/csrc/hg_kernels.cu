@@ -486,7 +486,7 @@ __global__ void k_validate_init(const double *mass, const double *x, const doubl
                                 int32_t *flag)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        bool ok = isfinite(mass[i]) && mass[i] > 0.0;
+        bool ok = isfinite(mass[i]) && mass[i] > 0.0 && mass[i] <= lim.mass;
         for (int k = 0; k < 3; ++k) ok = ok && within(x[3 * i + k], lim.pos) && within(v[3 * i + k], lim.deriv);
         if (!ok) atomicOr(flag, ERR_VALUE);
     }
@@ -496,7 +496,8 @@ __global__ void k_validate_state(const State st, int64_t n, double dt_min, doubl
                                  int32_t *flag)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        bool ok = isfinite(st.mass[i]) && st.mass[i] > 0.0 && isfinite(st.t[i]) && st.t[i] >= 0.0;
+        bool ok = isfinite(st.mass[i]) && st.mass[i] > 0.0 && st.mass[i] <= lim.mass && isfinite(st.t[i]) &&
+                  st.t[i] >= 0.0;
         for (int k = 0; k < 3; ++k) {
             const int64_t q = 3 * i + k;
             ok = ok && within(st.x[q], lim.pos) && within(st.v[q], lim.deriv) && within(st.a[q], lim.deriv) &&

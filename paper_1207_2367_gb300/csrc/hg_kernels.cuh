@@ -72,10 +72,24 @@ cudaError_t launch_angular_momentum(const State &st, int64_t n, double t, double
 // The mixed path's FP32 pair arithmetic squares position differences and forms
 // products of derivatives and differences, so its limits keep those in FP32's
 // range; the FP64 path's keep them in FP64's.
+// mass bounds the masses and the pair law's largest factors: every pair, the one
+// of a particle with itself included, has m_j / (r^2 + eps^2)^(3/2) <= m_j / eps^3
+// and m_j / (r^2 + eps^2) <= m_j / eps^2, kept below L = 1e37 in the mixed path
+// (FLT_MAX is 3.4e38) and L = 1e300 in the FP64 path by m <= L min(1, eps^3).
+// With eps = 0 the pairs at r = 0 are skipped and only m <= L applies.
 struct ValueLimits {
-    double pos, deriv;
+    double pos, deriv, mass;
 };
-inline ValueLimits value_limits(bool mixed) { return mixed ? ValueLimits{1e15, 1e30} : ValueLimits{1e150, 1e150}; }
+inline ValueLimits value_limits(bool mixed, double eps)
+{
+    const double L = mixed ? 1e37 : 1e300;
+    const double e3 = eps * eps * eps;
+    const double mass = eps > 0.0 && e3 < 1.0 ? L * e3 : L;
+    return mixed ? ValueLimits{1e15, 1e30, mass} : ValueLimits{1e150, 1e150, mass};
+}
+// eps^2 below this (or eps = 0) selects the evaluation that skips pairs whose
+// softened r^2 is zero: FP32 rounds such an eps^2 to zero.
+constexpr double kGuardEps2 = 0x1p-100;
 cudaError_t launch_validate_init(const double *mass, const double *x, const double *v, int64_t n,
                                  const ValueLimits &lim, int32_t *flag, cudaStream_t s);
 cudaError_t launch_validate_state(const State &st, int64_t n, double dt_min, double dt_max, const ValueLimits &lim,

@@ -229,7 +229,7 @@ extern "C" int hg_evaluate_static(int64_t n, const double *mass, const double *p
     a.plan_host = make_plan(m, pq);
     a.partial = reinterpret_cast<double *>(base + kRecBytes);
     a.eps2 = eps * eps;
-    a.guard = eps == 0.0 ? 1 : 0;
+    a.guard = eps * eps < kGuardEps2 ? 1 : 0;
     a.tx_extra = 0;
     a.err = err;
     a.direct_b1 = 0;        // partials summed by k_reduce

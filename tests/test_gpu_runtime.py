@@ -391,6 +391,43 @@ def test_mixed_context_refuses_values_outside_fp32_range(hg):
         hg.hg_free(ctx)
 
 
+def test_softening_bounds_the_masses(hg):
+    """With eps > 0 a pair's factor m_j / (r^2 + eps^2)^(3/2) is at most m_j / eps^3
+    (the pair of a particle with itself included): a mixed context refuses a mass
+    above 1e37 min(1, eps^3) (FP32 range), an FP64 one above 1e300 min(1, eps^3),
+    either an eps above its position limit.  An eps whose square FP32 rounds to zero takes the
+    evaluation that skips pairs at r^2 = 0: its results are finite and within the
+    mixed metric of the oracle."""
+    from gpu_util import gpu_eval
+    from test_gpu_parity import check_eval
+    n = 64
+    p = inputs.plummer(n, 31)                        # masses 1/64
+    mixed = hg.hg_default_opts(precision=hg.HG_MIXED, dt_max=DT_MAX)
+    fp64 = hg.hg_default_opts(precision=hg.HG_FP64, dt_max=DT_MAX)
+    for eps, o in ((1e-13, mixed), (1e-101, fp64), (1e16, mixed), (1e151, fp64)):
+        with pytest.raises(hg.HGError) as e:
+            hg.hg_init(p.mass, p.pos, p.vel, eps, 0.45, o)
+        assert e.value.code == hg.HG_EINVAL, eps
+    hg.hg_free(hg.hg_init(p.mass, p.pos, p.vel, 1e-12, 0.45, mixed))    # 1.6e34 <= 1e37
+    hg.hg_free(hg.hg_init(p.mass, p.pos, p.vel, 1e-100, 0.45, fp64))    # 1.6e298 <= 1e300
+    mass, eps = p.mass * 1e-25, 1e-20                # eps^2 = 1e-40: zero in FP32
+    ctx = hg.hg_init(mass, p.pos, p.vel, eps, 0.45, mixed)
+    try:
+        st, t0 = gpu_state(hg, ctx, n)
+        for f in hg.STATE_FIELDS:
+            assert np.isfinite(st[f]).all(), f
+        idx = np.arange(n)
+        got = gpu_eval(hg, ctx, idx, t0)
+        ref = oracle.evaluate(mass, st["pos"], st["vel"], st["acc"], eps, idx)
+        check_eval(got, ref, 1, oracle.eval_absum(mass, st["pos"], st["vel"], st["acc"], eps, idx))
+        hg.hg_step(ctx, 8)
+        st, _ = gpu_state(hg, ctx, n)
+        for f in hg.STATE_FIELDS:
+            assert np.isfinite(st[f]).all(), f
+    finally:
+        hg.hg_free(ctx)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_section_profile_changes_nothing_and_accounts_for_the_time(hg, precision):
     """opts.profile = 1 (CUDA events around the sections of every graph-replayed
