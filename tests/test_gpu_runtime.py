@@ -291,6 +291,40 @@ def test_bound_mixed_state_written_in_place(hg):
             hg.hg_free(ctx)
 
 
+@pytest.mark.parametrize("order", [6, 4])
+def test_fp32_copies_track_the_state(hg, order):
+    """The mixed predictor reads FP32 copies of v, the mass and the derivatives
+    that the corrector keeps beside the FP64 state.  After free block steps (the
+    copies maintained step by step, graph replays and an explicit step), a
+    second context handed the same state through hg_set_state (copies rebuilt
+    from the FP64 fields) takes the next block steps bitwise like the first."""
+    n, eps = 3000, 1e-3
+    p = inputs.plummer(n, 47)
+    o = hg.hg_default_opts(precision=hg.HG_MIXED, dt_max=DT_MAX, order=order)
+    a = hg.hg_init(p.mass, p.pos, p.vel, eps, 0.45, o)
+    b = hg.hg_init(p.mass, p.pos, p.vel, eps, 0.45, o)
+    try:
+        hg.hg_step(a, 30)
+        for _ in range(3):                               # explicit block steps
+            t_next, m = hg.hg_next_block(a)
+            hg.hg_predict(a, t_next)
+            hg.hg_evaluate(a, None, m)
+            hg.hg_correct(a, None, m)
+        hg.hg_step(a, 5)
+        st, t_sys = gpu_state(hg, a, n)
+        hg.hg_set_state(b, st, t_sys)
+        for ctx in (a, b):
+            hg.hg_step(ctx, 30)
+        ra, ta = gpu_state(hg, a, n)
+        rb, tb = gpu_state(hg, b, n)
+        assert ta == tb
+        for f in hg.STATE_FIELDS:
+            np.testing.assert_array_equal(ra[f], rb[f], err_msg=f)
+    finally:
+        for ctx in (a, b):
+            hg.hg_free(ctx)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_identical_contexts_stay_bitwise_identical(hg, precision):
     """Determinism: two contexts with the same input take 200 graph-replayed
