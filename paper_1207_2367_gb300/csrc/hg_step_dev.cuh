@@ -160,7 +160,8 @@ __device__ __forceinline__ void predict_record(const State &st, const Records &r
                 // series (its rounding, ~5e-7 of a term that is itself a small
                 // part of the step's displacement, stays far below the FP32 pair
                 // error), then split into float hi + lo: 3 FP64 instructions per
-                // component, the FP64 pipe being this kernel's limit on GB300.
+                // component (at 64 cycles per warp instruction the FP64 unit
+                // shares this kernel's limit with DRAM on GB300).
                 // Velocities and accelerations feed only the FP32 pair
                 // arithmetic: FP32 Horner series from the rounded derivatives.
                 // The FP32 inputs come rounded already (st.f32): the same
