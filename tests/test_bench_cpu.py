@@ -56,3 +56,23 @@ def test_kappa_statistics():
     assert abs(st["worst_particle_rel_err"] - 1e-5) < 1e-15        # particle 2: 1e-8 / 1e-3
     assert abs(st["worst_particle_kappa"] - 1e3) < 1e-9             # 1.0 / 1e-3
     assert abs(st["max_err_over_scale"] - 5e-8) < 1e-15            # particle 1: 1e-7 / 2
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference (the oracle on the host, no GPU): one JSON line
+    with the metric, a positive rate, the configuration and the keys the
+    reference arm carries (cpu_baseline describing the run, e2e with no copies)."""
+    import json
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0", "--n", "65536"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["value"] > 0 and line["unit"] == "interactions/s" and line["higher_is_better"] is True
+    assert line["steps"] == 1 and line["warmup"] == 0 and line["config"]["n"] == 65536
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "interactions/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
