@@ -168,44 +168,97 @@ struct Mixed {
         hi = t;
     }
 
-    // The pairs of one tile: ppt record pairs per lane, folded into the
-    // compensated sums every `fold`.  MASK: some lane's own record is in the tile
-    // (pair selfp[k], keep-mask selfk[k]); without it the noise scale needs no mask.
+    // Pair (i, record pair jp) of every i-particle of the lane.
     template <bool GUARD, bool MASK>
-    __device__ __forceinline__ static void tile_pairs(const float4 *a0, const float2 *a6, int ppt, int fold,
-                                                      int tpi, int lane_j, const ITile &iv, Acc &acc, f2_t eps2,
-                                                      const int (&selfp)[I], const f2_t (&selfk)[I])
+    __device__ __forceinline__ static void pair_step(const float4 *a0, const float2 *a6, int jp, const ITile &iv,
+                                                     f2_t eps2, const int (&selfp)[I], const f2_t (&selfk)[I],
+                                                     f2_t (&ch)[I][9], f2_t (&cn)[I])
     {
         const f2_t one2 = f2_pack(1.f, 1.f);
-        for (int g = 0; g < ppt; g += fold) {
-            f2_t ch[I][9], cn[I];
+        const float4 q0 = a0[jp], q1 = a0[TP + jp], q2 = a0[2 * TP + jp], q3 = a0[3 * TP + jp],
+                     q4 = a0[4 * TP + jp], q5 = a0[5 * TP + jp];
+        const float2 q6 = a6[jp];
 #pragma unroll
-            for (int k = 0; k < I; ++k) {
-                cn[k] = 0ull;
+        for (int k = 0; k < I; ++k)
+            pair<GUARD>(iv.d[k], q0, q1, q2, q3, q4, q5, q6, eps2, (MASK && jp == selfp[k]) ? selfk[k] : one2,
+                        ch[k], cn[k]);
+    }
+
+    // The pairs of one tile: TP / tpi record pairs per lane, folded into the
+    // compensated sums every kFold / 2.  MASK: some lane's own record is in the
+    // tile (pair selfp[k], keep-mask selfk[k]); without it the noise scale needs
+    // no mask.  TPI > 0: tpi known at compile time, so that the pairs of a fold
+    // are unrolled with constant shared-memory offsets (measured: 9 % faster than
+    // the loop with a run-time stride at tpi = 1); TPI = 0: any tpi.
+    template <bool GUARD, bool MASK, int TPI>
+    __device__ __forceinline__ static void tile_pairs(const float4 *a0, const float2 *a6, int tpi_rt, int lane_j,
+                                                      const ITile &iv, Acc &acc, f2_t eps2, const int (&selfp)[I],
+                                                      const f2_t (&selfk)[I])
+    {
+        constexpr int kF = kFold / 2;
+        if constexpr (TPI > 0) {
+            constexpr int kPpt = TP / TPI;                    // pairs per lane in this tile
+            constexpr int kU = kPpt < kF ? kPpt : kF;         // pairs per fold
+            const int lj = TPI == 1 ? 0 : lane_j;
+            for (int g = 0; g < kPpt; g += kU) {
+                f2_t ch[I][9], cn[I];
+                zero_chunk(ch, cn);
 #pragma unroll
-                for (int c = 0; c < 9; ++c) ch[k][c] = 0ull;
+                for (int u = 0; u < kU; ++u)
+                    pair_step<GUARD, MASK>(a0, a6, (g + u) * TPI + lj, iv, eps2, selfp, selfk, ch, cn);
+                fold_chunk(acc, ch, cn);
             }
-            for (int u = 0; u < fold; ++u) {
-                const int jp = (g + u) * tpi + lane_j;
-                const float4 q0 = a0[jp], q1 = a0[TP + jp], q2 = a0[2 * TP + jp], q3 = a0[3 * TP + jp],
-                             q4 = a0[4 * TP + jp], q5 = a0[5 * TP + jp];
-                const float2 q6 = a6[jp];
-#pragma unroll
-                for (int k = 0; k < I; ++k)
-                    pair<GUARD>(iv.d[k], q0, q1, q2, q3, q4, q5, q6, eps2,
-                                (MASK && jp == selfp[k]) ? selfk[k] : one2, ch[k], cn[k]);
-            }
-#pragma unroll
-            for (int k = 0; k < I; ++k) {
-                const float2 nn = f2_unpack(cn[k]);
-                acc.n[k] += nn.x + nn.y;
-#pragma unroll
-                for (int c = 0; c < 9; ++c) {
-                    const float2 v = f2_unpack(ch[k][c]);
-                    kahan(acc.hi[k][c], acc.lo[k][c], v.x + v.y);
-                }
+        } else {
+            const int ppt = TP >> (__ffs(tpi_rt) - 1);        // tpi a power of two
+            const int fold = ppt < kF ? ppt : kF;
+            for (int g = 0; g < ppt; g += fold) {
+                f2_t ch[I][9], cn[I];
+                zero_chunk(ch, cn);
+                for (int u = 0; u < fold; ++u)
+                    pair_step<GUARD, MASK>(a0, a6, (g + u) * tpi_rt + lane_j, iv, eps2, selfp, selfk, ch, cn);
+                fold_chunk(acc, ch, cn);
             }
         }
+    }
+
+    __device__ __forceinline__ static void zero_chunk(f2_t (&ch)[I][9], f2_t (&cn)[I])
+    {
+#pragma unroll
+        for (int k = 0; k < I; ++k) {
+            cn[k] = 0ull;
+#pragma unroll
+            for (int c = 0; c < 9; ++c) ch[k][c] = 0ull;
+        }
+    }
+
+    // The FP32 chunk sums of a fold into the compensated sums.
+    __device__ __forceinline__ static void fold_chunk(Acc &acc, const f2_t (&ch)[I][9], const f2_t (&cn)[I])
+    {
+#pragma unroll
+        for (int k = 0; k < I; ++k) {
+            const float2 nn = f2_unpack(cn[k]);
+            acc.n[k] += nn.x + nn.y;
+#pragma unroll
+            for (int c = 0; c < 9; ++c) {
+                const float2 v = f2_unpack(ch[k][c]);
+                kahan(acc.hi[k][c], acc.lo[k][c], v.x + v.y);
+            }
+        }
+    }
+
+    template <bool GUARD, bool MASK>
+    __device__ __forceinline__ static void tile_by_tpi(const float4 *a0, const float2 *a6, int tpi, int lane_j,
+                                                       const ITile &iv, Acc &acc, f2_t eps2, const int (&selfp)[I],
+                                                       const f2_t (&selfk)[I])
+    {
+        if (tpi == 1)
+            tile_pairs<GUARD, MASK, 1>(a0, a6, tpi, lane_j, iv, acc, eps2, selfp, selfk);
+        else if (tpi == 2)
+            tile_pairs<GUARD, MASK, 2>(a0, a6, tpi, lane_j, iv, acc, eps2, selfp, selfk);
+        else if (tpi == 4)
+            tile_pairs<GUARD, MASK, 4>(a0, a6, tpi, lane_j, iv, acc, eps2, selfp, selfk);
+        else
+            tile_pairs<GUARD, MASK, 0>(a0, a6, tpi, lane_j, iv, acc, eps2, selfp, selfk);
     }
 
     // tile: absolute index of the j-tile, to find the pair holding each
@@ -229,12 +282,10 @@ struct Mixed {
             selfk[k] = (r & 1) ? f2_pack(1.f, 0.f) : f2_pack(0.f, 1.f);
             mine = mine || selfp[k] >= 0;
         }
-        const int ppt = TP >> (__ffs(tpi) - 1);   // pairs per lane in this tile (tpi a power of two)
-        const int fold = ppt < kFold / 2 ? ppt : kFold / 2;
         if (__any_sync(0xffffffffu, mine))
-            tile_pairs<GUARD, true>(a0, a6, ppt, fold, tpi, lane_j, iv, acc, eps2, selfp, selfk);
+            tile_by_tpi<GUARD, true>(a0, a6, tpi, lane_j, iv, acc, eps2, selfp, selfk);
         else
-            tile_pairs<GUARD, false>(a0, a6, ppt, fold, tpi, lane_j, iv, acc, eps2, selfp, selfk);
+            tile_by_tpi<GUARD, false>(a0, a6, tpi, lane_j, iv, acc, eps2, selfp, selfk);
     }
 
     // Compensated pairs (true value hi - lo) added without rounding loss in hi:
