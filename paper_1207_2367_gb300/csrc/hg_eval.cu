@@ -246,6 +246,8 @@ struct Mixed {
         }
     }
 
+    // Compile-time strides for 1, 2 and 4 threads per particle (the plans of large
+    // blocks); copies for every tpi up to 64 measured slower everywhere (more code).
     template <bool GUARD, bool MASK>
     __device__ __forceinline__ static void tile_by_tpi(const float4 *a0, const float2 *a6, int tpi, int lane_j,
                                                        const ITile &iv, Acc &acc, f2_t eps2, const int (&selfp)[I],
